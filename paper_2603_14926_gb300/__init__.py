@@ -1,0 +1,385 @@
+"""paper_2603_14926_gb300 -- branch-free multicomponent arithmetic on GB300.
+
+Thin Python binding over libmpgpu.so (C ABI declared in include/mpgpu.h): every
+function here only checks shapes, picks plane strides and the current CUDA
+stream, and calls the library entry point of the same name.  All arithmetic
+runs in the library's CUDA kernels; there is no fallback.  PyTorch provides the
+device memory and streams.
+
+Numbers are "K-arrays": torch tensors of shape (K, ...) on a CUDA device,
+float64 for dd/ddc/td/qd and float32 for ds/tf/qf, each component plane
+contiguous (component 0 leading).  Complex K-arrays have 2K planes.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PRECS = {"dd": (2, "float64"), "ddc": (2, "float64"), "td": (3, "float64"),
+         "qd": (4, "float64"), "ds": (2, "float32"), "tf": (3, "float32"),
+         "qf": (4, "float32")}
+DK_PRECS = ("dd", "ddc", "td", "qd")
+# per-polynomial solver status codes (mp_roots_P)
+DK_CAP, DK_CONVERGED, DK_STAGNATED, DK_TIMEOUT, DK_BREAKDOWN = 0, 1, 2, 3, 4
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small",
+          4: "watchdog expired", 5: "not supported"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmpgpu.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class MPError(RuntimeError):
+    def __init__(self, fn, code, cuda=0):
+        super().__init__(f"{fn}: {STATUS.get(code, code)}" + (f" (cudaError {cuda})" if cuda else ""))
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+
+    return _b.build(force=force)
+
+
+_i64, _i32, _vp, _dbl, _int = ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+
+
+class RootsOpts(ctypes.Structure):
+    """mp_roots_opts (include/mpgpu.h)."""
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("stag_window", ctypes.c_int32), ("stag_min_iter", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("radius", ctypes.c_double),
+                ("watchdog_cycles", ctypes.c_int64), ("max_degree", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("sort", ctypes.c_int32)]
+
+
+def _declare(L):
+    for p in PRECS:
+        sigs = {
+            "add": [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp],
+            "mul": [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp],
+            "recip": [_i64, _vp, _i64, _vp, _i64, _vp],
+            "axpy": [_i64, _vp, _vp, _i64, _vp, _i64, _vp],
+            "dot": [_i64, _vp, _i64, _vp, _i64, _vp, _vp, ctypes.c_size_t, _vp],
+            "gemv": [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp],
+            "gemm": [_int, _int, _i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64,
+                     _i64, _vp],
+            "gemm_ex": [_int, _int, _i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp,
+                        _i64, _i64, _int, _vp],
+            "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
+            "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                                  _vp, _i64, _vp],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, f"mp_{name}_{p}", None)
+            if f is None:
+                continue
+            f.argtypes = args
+            f.restype = _int
+        getattr(L, f"mp_dot_workspace_{p}").argtypes = [_i64]
+        getattr(L, f"mp_dot_workspace_{p}").restype = ctypes.c_size_t
+        getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
+        getattr(L, f"mp_gemm_config_name_{p}").argtypes = [_int]
+        getattr(L, f"mp_gemm_config_name_{p}").restype = ctypes.c_char_p
+    for p in DK_PRECS:
+        f = getattr(L, f"mp_poly_from_roots_{p}", None)
+        if f is None:
+            continue
+        f.argtypes = [_i64, _vp, _vp, _vp, _vp, _i64, _vp]
+        f.restype = _int
+        f = getattr(L, f"mp_roots_init_{p}")
+        f.argtypes = [_i64, _vp, _vp, _i64, _dbl, _i32, _vp, _i64, _vp]
+        f.restype = _int
+        f = getattr(L, f"mp_roots_workspace_{p}")
+        f.argtypes = [_i64]
+        f.restype = ctypes.c_size_t
+        getattr(L, f"mp_roots_max_degree_{p}").restype = _i32
+        f = getattr(L, f"mp_roots_{p}")
+        f.argtypes = [_i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp,
+                      ctypes.POINTER(RootsOpts), _vp, ctypes.c_size_t, _vp]
+        f.restype = _int
+    L.mp_peak_run.argtypes = [_int, _i64, _int, _int, ctypes.POINTER(ctypes.c_float),
+                              ctypes.POINTER(ctypes.c_double), _vp]
+    L.mp_peak_run.restype = _int
+    L.mp_status_str.restype = ctypes.c_char_p
+    L.mp_version.restype = ctypes.c_char_p
+    L.mp_last_cuda_error.restype = _int
+    L.mp_sm_count.restype = _int
+
+
+def load():
+    """Load libmpgpu.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run paper_2603_14926_gb300.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+        return _lib
+
+
+def lib():
+    return _lib if _lib is not None else load()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream():
+    return _torch().cuda.current_stream().cuda_stream
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != 0:
+        raise MPError(name, rc, lib().mp_last_cuda_error() if rc == 2 else 0)
+
+
+def _dtype(prec):
+    t = _torch()
+    return t.float64 if PRECS[prec][1] == "float64" else t.float32
+
+
+def _check(prec, x, name, ndim=None):
+    t = _torch()
+    K = PRECS[prec][0]
+    if not isinstance(x, t.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if x.dtype != _dtype(prec):
+        raise TypeError(f"{name}: expected {_dtype(prec)} for {prec}, got {x.dtype}")
+    if x.shape[0] != K:
+        raise ValueError(f"{name}: expected {K} component planes, got shape {tuple(x.shape)}")
+    if ndim is not None and x.dim() != ndim:
+        raise ValueError(f"{name}: expected {ndim} dims, got {tuple(x.shape)}")
+    if not x[0].is_contiguous():
+        raise ValueError(f"{name}: each component plane must be contiguous")
+    return x
+
+
+def _ps(x):
+    """Plane stride in elements."""
+    return x.stride(0) if x.shape[0] > 1 else x[0].numel()
+
+
+def _ptr(x):
+    return None if x is None else x.data_ptr()
+
+
+def empty(prec, *shape, device="cuda"):
+    K = PRECS[prec][0]
+    return _torch().empty((K, *shape), dtype=_dtype(prec), device=device)
+
+
+def zeros(prec, *shape, device="cuda"):
+    K = PRECS[prec][0]
+    return _torch().zeros((K, *shape), dtype=_dtype(prec), device=device)
+
+
+# ---------------------------------------------------------------------------
+# elementwise, AXPY, dot, GEMV, GEMM
+# ---------------------------------------------------------------------------
+
+def _ew(name, prec, a, b=None, out=None):
+    _check(prec, a, "a")
+    if b is not None:
+        _check(prec, b, "b")
+        if b.shape != a.shape:
+            raise ValueError("a and b differ in shape")
+    out = empty(prec, *a.shape[1:], device=a.device) if out is None else _check(prec, out, "out")
+    n = a[0].numel()
+    if b is None:
+        _call(f"mp_{name}_{prec}", n, _ptr(a), _ps(a), _ptr(out), _ps(out), _stream())
+    else:
+        _call(f"mp_{name}_{prec}", n, _ptr(a), _ps(a), _ptr(b), _ps(b), _ptr(out), _ps(out),
+              _stream())
+    return out
+
+
+def add(prec, a, b, out=None):
+    return _ew("add", prec, a, b, out)
+
+
+def mul(prec, a, b, out=None):
+    return _ew("mul", prec, a, b, out)
+
+
+def recip(prec, a, out=None):
+    return _ew("recip", prec, a, None, out)
+
+
+def axpy(prec, alpha, x, y):
+    """y := alpha * x + y in place; alpha is a sequence of K host numbers."""
+    _check(prec, x, "x")
+    _check(prec, y, "y")
+    K = PRECS[prec][0]
+    ct = ctypes.c_double if PRECS[prec][1] == "float64" else ctypes.c_float
+    al = (ct * K)(*[float(v) for v in alpha])
+    _call(f"mp_axpy_{prec}", x[0].numel(), ctypes.cast(al, _vp), _ptr(x), _ps(x), _ptr(y), _ps(y),
+          _stream())
+    return y
+
+
+def dot_workspace(prec, n):
+    return int(getattr(lib(), f"mp_dot_workspace_{prec}")(n))
+
+
+def dot(prec, x, y, out=None, ws=None):
+    _check(prec, x, "x")
+    _check(prec, y, "y")
+    t = _torch()
+    n = x[0].numel()
+    K = PRECS[prec][0]
+    out = empty(prec, device=x.device) if out is None else out
+    nb = dot_workspace(prec, n)
+    if ws is None:
+        ws = t.empty(nb, dtype=t.uint8, device=x.device)
+    _call(f"mp_dot_{prec}", n, _ptr(x), _ps(x), _ptr(y), _ps(y), _ptr(out), _ptr(ws),
+          ws.numel() * ws.element_size(), _stream())
+    return out.reshape(K)
+
+
+def gemv(prec, A, x, out=None):
+    _check(prec, A, "A", 3)
+    _check(prec, x, "x", 2)
+    K, m, n = A.shape
+    if A[0].stride(1) != 1:
+        raise ValueError("A rows must be contiguous")
+    out = empty(prec, m, device=A.device) if out is None else out
+    _call(f"mp_gemv_{prec}", m, n, _ptr(A), A[0].stride(0), _ps(A), _ptr(x), _ps(x), _ptr(out),
+          _ps(out), _stream())
+    return out
+
+
+def gemm_num_configs(prec):
+    return int(getattr(lib(), f"mp_gemm_num_configs_{prec}")())
+
+
+def gemm_config_name(prec, c):
+    return getattr(lib(), f"mp_gemm_config_name_{prec}")(c).decode()
+
+
+def gemm(prec, A, B, opA=0, opB=0, out=None, config=-1):
+    """C := op(A) op(B).  A is (K, m, k) for opA=0 or (K, k, m) for opA=1; likewise B."""
+    _check(prec, A, "A", 3)
+    _check(prec, B, "B", 3)
+    m, k = (A.shape[1], A.shape[2]) if not opA else (A.shape[2], A.shape[1])
+    k2, n = (B.shape[1], B.shape[2]) if not opB else (B.shape[2], B.shape[1])
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} vs {k2}")
+    for X, nm in ((A, "A"), (B, "B")):
+        if X[0].stride(1) != 1:
+            raise ValueError(f"{nm} rows must be contiguous")
+    out = empty(prec, m, n, device=A.device) if out is None else _check(prec, out, "out", 3)
+    _call(f"mp_gemm_ex_{prec}", int(opA), int(opB), m, n, k, _ptr(A), A[0].stride(0), _ps(A),
+          _ptr(B), B[0].stride(0), _ps(B), _ptr(out), out[0].stride(0), _ps(out), int(config),
+          _stream())
+    return out
+
+
+# ---------------------------------------------------------------------------
+# polynomials and roots
+# ---------------------------------------------------------------------------
+
+def polyeval(prec, coef_off, coef, npts, x_re, x_im=None):
+    """Batched Horner; coef_off is a CUDA int64 tensor (npoly+1)."""
+    _check(prec, coef, "coef", 2)
+    _check(prec, x_re, "x_re", 2)
+    npoly = coef_off.numel() - 1
+    y_re = empty(prec, npoly * npts, device=coef.device)
+    y_im = None
+    if x_im is not None:
+        _check(prec, x_im, "x_im", 2)
+        y_im = empty(prec, npoly * npts, device=coef.device)
+    _call(f"mp_polyeval_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), npts, _ptr(x_re),
+          _ptr(x_im), _ps(x_re), _ptr(y_re), _ptr(y_im), _ps(y_re), _stream())
+    return (y_re, y_im) if x_im is not None else y_re
+
+
+def polyeval_backward(prec, coef_off, coef, npts, x, dy, want_dcoef=True, want_dx=True):
+    _check(prec, coef, "coef", 2)
+    _check(prec, x, "x", 2)
+    _check(prec, dy, "dy", 2)
+    npoly = coef_off.numel() - 1
+    dcoef = empty(prec, coef.shape[1], device=coef.device) if want_dcoef else None
+    dx = empty(prec, x.shape[1], device=coef.device) if want_dx else None
+    _call(f"mp_polyeval_backward_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), npts,
+          _ptr(x), _ps(x), _ptr(dy), _ps(dy), _ptr(dcoef), _ps(dcoef) if dcoef is not None else 0,
+          _ptr(dx), _ps(dx) if dx is not None else 0, _stream())
+    return dcoef, dx
+
+
+def poly_from_roots(prec, coef_off, rootdata, delta):
+    """Coefficients of the root-solving workload (see inputs.DKProblem)."""
+    K = PRECS[prec][0]
+    npoly = coef_off.numel() - 1
+    total = int(coef_off[-1].item()) if coef_off.is_cuda else int(coef_off[-1])
+    coef = empty(prec, total, device=rootdata.device)
+    _call(f"mp_poly_from_roots_{prec}", npoly, _ptr(coef_off), _ptr(rootdata), _ptr(delta),
+          _ptr(coef), _ps(coef), _stream())
+    return coef
+
+
+def roots_init(prec, coef_off, coef, max_degree, radius=0.0):
+    _check(prec, coef, "coef", 2)
+    K = PRECS[prec][0]
+    npoly = coef_off.numel() - 1
+    total = coef.shape[1] - npoly
+    z = _torch().zeros((2 * K, max(total, 1)), dtype=coef.dtype, device=coef.device)
+    _call(f"mp_roots_init_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), float(radius),
+          int(max_degree), _ptr(z), z.stride(0), _stream())
+    return z[:, :total]
+
+
+def roots_workspace(prec, npoly):
+    return int(getattr(lib(), f"mp_roots_workspace_{prec}")(npoly))
+
+
+def roots_max_degree(prec):
+    return int(getattr(lib(), f"mp_roots_max_degree_{prec}")())
+
+
+def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_window=0,
+          stag_min_iter=0, mode=0, radius=0.0, watchdog_cycles=0, threads=0, blocks_per_sm=0,
+          sort=0, out=None, ws=None):
+    """Durand-Kerner on every polynomial; returns (roots (2K, total), iters, status)."""
+    t = _torch()
+    _check(prec, coef, "coef", 2)
+    K = PRECS[prec][0]
+    npoly = coef_off.numel() - 1
+    total = coef.shape[1] - npoly
+    dev = coef.device
+    r = t.zeros((2 * K, max(total, 1)), dtype=coef.dtype, device=dev) if out is None else out
+    iters = t.zeros(npoly, dtype=t.int32, device=dev)
+    status = t.zeros(npoly, dtype=t.int32, device=dev)
+    nb = roots_workspace(prec, npoly)
+    if ws is None:
+        ws = t.empty(max(nb, 1), dtype=t.uint8, device=dev)
+    o = RootsOpts(tol, max_iter, stag_window, stag_min_iter, mode, radius, watchdog_cycles,
+                  int(max_degree), threads, blocks_per_sm, sort)
+    _call(f"mp_roots_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), _ptr(z0),
+          z0.stride(0) if z0 is not None else 0, _ptr(r), r.stride(0), _ptr(iters),
+          _ptr(status), ctypes.byref(o), _ptr(ws), ws.numel(), _stream())
+    return r[:, :total], iters, status
+
+
+def peak(kind, iters=4096, blocks=None, threads=256):
+    """Pipe-peak microbenchmark: returns (lane instructions per second, ms)."""
+    L = lib()
+    blocks = blocks or L.mp_sm_count() * 8
+    ms, ops = ctypes.c_float(), ctypes.c_double()
+    _call("mp_peak_run", kind, iters, blocks, threads, ctypes.byref(ms), ctypes.byref(ops),
+          _stream())
+    return ops.value / (ms.value * 1e-3), ms.value

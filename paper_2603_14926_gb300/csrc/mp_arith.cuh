@@ -1,0 +1,397 @@
+// mp_arith.cuh -- branch-free multicomponent arithmetic on the CUDA cores.
+//
+// Device restatement of Kouya, arXiv 2603.14926, Section 2:
+//   Algorithms 1-3  (QuickTwoSum, TwoSum, FMA TwoProd)
+//   Algorithms 4, 6 (DWAdd sloppy, DWBFAdd), 7, 8 (DWMul, DWBFMul)
+//   Algorithms 11, 12 (TWBFAdd, TWBFMul), 13, 14 (QWBFAdd, QDBFMul)
+// on binary64 (FP64 pipe) or binary32 (FP32 pipe) components.
+//
+// Every floating-point step is an explicit round-to-nearest-even intrinsic
+// (__dadd_rn/__dsub_rn/__dmul_rn/__fma_rn and the binary32 forms), so the
+// compiler can neither contract a*b+c nor reassociate: each algorithm runs as
+// exactly the operation sequence the paper prints.  Negation and the "-p" of
+// TwoProd's FMA are sign-operand modifiers, not instructions.  Tensor cores
+// are not used: an FP64 DMMA returns no rounding error, which every step here
+// needs.
+#pragma once
+#include <cstdint>
+
+namespace mp {
+
+template <typename T> struct fpu;
+
+template <> struct fpu<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
+template <> struct fpu<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+
+// ---------------------------------------------------------------------------
+// Algorithms 1-3
+// ---------------------------------------------------------------------------
+
+// Algorithm 1: s = a + b, e = b - (s - a); exact when |a| >= |b|.
+template <typename T>
+__device__ __forceinline__ void quick_two_sum(T a, T b, T &s, T &e)
+{
+    using F = fpu<T>;
+    T s_ = F::add(a, b);
+    e = F::sub(b, F::sub(s_, a));
+    s = s_;
+}
+
+// Algorithm 2: s = a + b, v = s - a, e = (a - (s - v)) + (b - v); exact.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
+{
+    using F = fpu<T>;
+    T s_ = F::add(a, b);
+    T v = F::sub(s_, a);
+    e = F::add(F::sub(a, F::sub(s_, v)), F::sub(b, v));
+    s = s_;
+}
+
+// Algorithm 3: p = a * b, e = FMA(a, b, -p); exact.
+template <typename T>
+__device__ __forceinline__ void two_prod(T a, T b, T &p, T &e)
+{
+    using F = fpu<T>;
+    T p_ = F::mul(a, b);
+    e = F::fma(a, b, -p_);
+    p = p_;
+}
+
+// A K-component number, component 0 leading.  Always held in registers.
+template <typename T, int K> struct mpv {
+    T c[K];
+};
+
+// ---------------------------------------------------------------------------
+// Double word
+// ---------------------------------------------------------------------------
+
+// Algorithm 4 (DWAdd, the sloppy add of the QD library)
+template <typename T>
+__device__ __forceinline__ mpv<T, 2> dw_add_sloppy(const mpv<T, 2> &a, const mpv<T, 2> &b)
+{
+    using F = fpu<T>;
+    T s, e;
+    two_sum(a.c[0], b.c[0], s, e);
+    e = F::add(e, F::add(a.c[1], b.c[1]));
+    mpv<T, 2> r;
+    quick_two_sum(s, e, r.c[0], r.c[1]);
+    return r;
+}
+
+// Algorithm 6 (DWBFAdd)
+template <typename T>
+__device__ __forceinline__ mpv<T, 2> dw_add_bf(const mpv<T, 2> &a, const mpv<T, 2> &b)
+{
+    using F = fpu<T>;
+    T g1, g1e, g2, g2e, g3, g3e;
+    two_sum(a.c[0], b.c[0], g1, g1e);
+    two_sum(a.c[1], b.c[1], g2, g2e);
+    quick_two_sum(g1, g2, g3, g3e);
+    T g4 = F::add(g1e, g2e);
+    T g5 = F::add(g4, g3e);
+    mpv<T, 2> r;
+    quick_two_sum(g3, g5, r.c[0], r.c[1]);
+    return r;
+}
+
+// Algorithm 7 (DWMul; its undefined "QuickTwoProd" read as QuickTwoSum) and
+// Algorithm 8 (DWBFMul) are the same operation sequence:
+// (p00, pe00) = TwoProd(a0, b0); g1 = a0*b1 + a1*b0; g2 = pe00 + g1; QuickTwoSum(p00, g2).
+template <typename T>
+__device__ __forceinline__ mpv<T, 2> dw_mul_bf(const mpv<T, 2> &a, const mpv<T, 2> &b)
+{
+    using F = fpu<T>;
+    T p00, pe00;
+    two_prod(a.c[0], b.c[0], p00, pe00);
+    T p01 = F::mul(a.c[0], b.c[1]);
+    T p10 = F::mul(a.c[1], b.c[0]);
+    T g1 = F::add(p01, p10);
+    T g2 = F::add(pe00, g1);
+    mpv<T, 2> r;
+    quick_two_sum(p00, g2, r.c[0], r.c[1]);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Triple word
+// ---------------------------------------------------------------------------
+
+// Algorithm 11 (TWBFAdd)
+template <typename T>
+__device__ __forceinline__ mpv<T, 3> tw_add_bf(const mpv<T, 3> &A, const mpv<T, 3> &B)
+{
+    using F = fpu<T>;
+    T a1, b1, c1, d1, e1, f1, a2, c2, d2, e2, a3, d3, b3, c3, c5, d5, b6, c6, b7;
+    mpv<T, 3> r;
+    two_sum(A.c[0], B.c[0], a1, b1);
+    two_sum(A.c[1], B.c[1], c1, d1);
+    two_sum(A.c[2], B.c[2], e1, f1);
+    quick_two_sum(a1, c1, a2, c2);
+    T b2 = F::add(b1, f1);
+    two_sum(d1, e1, d2, e2);
+    quick_two_sum(a2, d2, a3, d3);
+    two_sum(b2, c2, b3, c3);
+    T c4 = F::add(c3, e2);
+    two_sum(c4, d3, c5, d5);
+    two_sum(b3, c5, b6, c6);
+    quick_two_sum(a3, b6, r.c[0], b7);
+    T c7 = F::add(c6, d5);
+    quick_two_sum(b7, c7, r.c[1], r.c[2]);
+    return r;
+}
+
+// Algorithm 12 (TWBFMul)
+template <typename T>
+__device__ __forceinline__ mpv<T, 3> tw_mul_bf(const mpv<T, 3> &A, const mpv<T, 3> &B)
+{
+    using F = fpu<T>;
+    T a0, b0, c0, e0, d0, f0, c1, d1, b2, c2, a3, b3, b5, c5, b6;
+    mpv<T, 3> r;
+    two_prod(A.c[0], B.c[0], a0, b0);
+    two_prod(A.c[0], B.c[1], c0, e0);
+    two_prod(A.c[1], B.c[0], d0, f0);
+    T g0 = F::mul(A.c[0], B.c[2]);
+    T h0 = F::mul(A.c[1], B.c[1]);
+    T i0 = F::mul(A.c[2], B.c[0]);
+    two_sum(c0, d0, c1, d1);
+    T e1 = F::add(e0, f0);
+    T g1 = F::add(g0, i0);
+    two_sum(b0, c1, b2, c2);
+    T g2 = F::add(g1, h0);
+    quick_two_sum(a0, b2, a3, b3);
+    T c3 = F::add(c2, d1);
+    T e3 = F::add(e1, g2);
+    T c4 = F::add(c3, e3);
+    quick_two_sum(b3, c4, b5, c5);
+    quick_two_sum(a3, b5, r.c[0], b6);
+    quick_two_sum(b6, c5, r.c[1], r.c[2]);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Quad word
+// ---------------------------------------------------------------------------
+
+// Algorithm 13 (QWBFAdd)
+template <typename T>
+__device__ __forceinline__ mpv<T, 4> qw_add_bf(const mpv<T, 4> &A, const mpv<T, 4> &B)
+{
+    using F = fpu<T>;
+    T a1, b1, c1, d1, e1, f1, g1, h1, a2, c2, d2, e2, f2, g2, b3, g3, c3, d3, e3, f3,
+        a4, c4, d4, e4, b5, d5, b6, c6, d6, e6, a7, b7, c7, d7, b8, c8, b10, c10, d10, c11;
+    mpv<T, 4> r;
+    two_sum(A.c[0], B.c[0], a1, b1);
+    two_sum(A.c[1], B.c[1], c1, d1);
+    two_sum(A.c[2], B.c[2], e1, f1);
+    two_sum(A.c[3], B.c[3], g1, h1);
+    quick_two_sum(a1, c1, a2, c2);
+    T b2 = F::add(b1, h1);
+    two_sum(d1, e1, d2, e2);
+    two_sum(f1, g1, f2, g2);
+    two_sum(b2, g2, b3, g3);
+    quick_two_sum(c2, d2, c3, d3);
+    two_sum(e2, f2, e3, f3);
+    quick_two_sum(a2, c3, a4, c4);
+    quick_two_sum(d3, e3, d4, e4);
+    two_sum(b3, d4, b5, d5);
+    T e5 = F::add(e4, f3);
+    two_sum(b5, c4, b6, c6);
+    two_sum(d5, e5, d6, e6);
+    quick_two_sum(a4, b6, a7, b7);
+    quick_two_sum(c6, d6, c7, d7);
+    T e8 = F::add(e6, g3);
+    quick_two_sum(b7, c7, b8, c8);
+    T d9 = F::add(d7, e8);
+    quick_two_sum(a7, b8, r.c[0], b10);
+    quick_two_sum(c8, d9, c10, d10);
+    quick_two_sum(b10, c10, r.c[1], c11);
+    quick_two_sum(c11, d10, r.c[2], r.c[3]);
+    return r;
+}
+
+// Algorithm 14 (QDBFMul)
+template <typename T>
+__device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 4> &B)
+{
+    using F = fpu<T>;
+    T a0, b0, c0, e0, d0, f0, g0, j0, h0, k0, i0, l0, c1, d1, e1, f1, g1, i1, b2, c2, e2, h2,
+        a3, b3, c3, d3, e3, g3, c4, e4, c6, d6, b7, c7, b8, c8, d8, c9;
+    mpv<T, 4> r;
+    two_prod(A.c[0], B.c[0], a0, b0);
+    two_prod(A.c[0], B.c[1], c0, e0);
+    two_prod(A.c[1], B.c[0], d0, f0);
+    two_prod(A.c[0], B.c[2], g0, j0);
+    two_prod(A.c[1], B.c[1], h0, k0);
+    two_prod(A.c[2], B.c[0], i0, l0);
+    T m0 = F::mul(A.c[0], B.c[3]);
+    T n0 = F::mul(A.c[1], B.c[2]);
+    T o0 = F::mul(A.c[2], B.c[1]);
+    T p0 = F::mul(A.c[3], B.c[0]);
+    two_sum(c0, d0, c1, d1);
+    two_sum(e0, f0, e1, f1);
+    two_sum(g0, i0, g1, i1);
+    T j1 = F::add(j0, l0);
+    T m1 = F::add(m0, p0);
+    T n1 = F::add(n0, o0);
+    two_sum(b0, c1, b2, c2);
+    two_sum(e1, h0, e2, h2);
+    T f2 = F::add(f1, j1);
+    T i2 = F::add(i1, k0);
+    T m2 = F::add(m1, n1);
+    quick_two_sum(a0, b2, a3, b3);
+    quick_two_sum(c2, d1, c3, d3);
+    two_sum(e2, g1, e3, g3);
+    T f3 = F::add(f2, m2);
+    T h3 = F::add(h2, i2);
+    two_sum(c3, e3, c4, e4);
+    T d4 = F::add(d3, h3);
+    T f4 = F::add(f3, g3);
+    T d5 = F::add(d4, e4);
+    two_sum(c4, d5, c6, d6);
+    two_sum(b3, c6, b7, c7);
+    T d7 = F::add(d6, f4);
+    quick_two_sum(a3, b7, r.c[0], b8);
+    two_sum(c7, d7, c8, d8);
+    two_sum(b8, c8, r.c[1], c9);
+    quick_two_sum(c9, d8, r.c[2], r.c[3]);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Precision tags: component type, K, add, multiply, reciprocal Newton steps.
+// ---------------------------------------------------------------------------
+
+#define MP_PREC_TAG(NAME, TYPE, KK, ADDF, MULF, NEWTON, FP64PIPE)                             \
+    struct NAME {                                                                           \
+        using T = TYPE;                                                                     \
+        static constexpr int K = KK;                                                        \
+        static constexpr int newton_steps = NEWTON;                                         \
+        static constexpr bool fp64 = FP64PIPE;                                              \
+        using V = mpv<TYPE, KK>;                                                            \
+        static __device__ __forceinline__ V add(const V &a, const V &b) { return ADDF(a, b); } \
+        static __device__ __forceinline__ V mul(const V &a, const V &b) { return MULF(a, b); } \
+    };
+
+MP_PREC_TAG(P_dd, double, 2, dw_add_bf<double>, dw_mul_bf<double>, 2, true)
+MP_PREC_TAG(P_ddc, double, 2, dw_add_sloppy<double>, dw_mul_bf<double>, 2, true)
+MP_PREC_TAG(P_td, double, 3, tw_add_bf<double>, tw_mul_bf<double>, 2, true)
+MP_PREC_TAG(P_qd, double, 4, qw_add_bf<double>, qw_mul_bf<double>, 3, true)
+MP_PREC_TAG(P_ds, float, 2, dw_add_bf<float>, dw_mul_bf<float>, 2, false)
+MP_PREC_TAG(P_tf, float, 3, tw_add_bf<float>, tw_mul_bf<float>, 2, false)
+MP_PREC_TAG(P_qf, float, 4, qw_add_bf<float>, qw_mul_bf<float>, 3, false)
+#undef MP_PREC_TAG
+
+// ---------------------------------------------------------------------------
+// Helpers over K-component values
+// ---------------------------------------------------------------------------
+
+template <class P> __device__ __forceinline__ typename P::V vzero()
+{
+    typename P::V r;
+#pragma unroll
+    for (int c = 0; c < P::K; c++) r.c[c] = typename P::T(0);
+    return r;
+}
+
+template <class P> __device__ __forceinline__ typename P::V vone()
+{
+    typename P::V r = vzero<P>();
+    r.c[0] = typename P::T(1);
+    return r;
+}
+
+// Subtraction = negate every component of b, then add (Section 2).
+template <class P> __device__ __forceinline__ typename P::V vneg(const typename P::V &a)
+{
+    typename P::V r;
+#pragma unroll
+    for (int c = 0; c < P::K; c++) r.c[c] = -a.c[c];
+    return r;
+}
+
+template <class P>
+__device__ __forceinline__ typename P::V vsub(const typename P::V &a, const typename P::V &b)
+{
+    return P::add(a, vneg<P>(b));
+}
+
+// Load / store element i of a K-array in plane layout (component c at base[c*ps + i]).
+template <class P>
+__device__ __forceinline__ typename P::V vload(const typename P::T *__restrict__ base, int64_t ps,
+                                               int64_t i)
+{
+    typename P::V r;
+#pragma unroll
+    for (int c = 0; c < P::K; c++) r.c[c] = base[c * ps + i];
+    return r;
+}
+
+template <class P>
+__device__ __forceinline__ void vstore(typename P::T *__restrict__ base, int64_t ps, int64_t i,
+                                       const typename P::V &v)
+{
+#pragma unroll
+    for (int c = 0; c < P::K; c++) base[c * ps + i] = v.c[c];
+}
+
+// Reciprocal by Newton's method (Section 2 leaves the scheme open): y0 = 1/x[0]
+// (one correctly rounded division), then newton_steps times e = 1 - x*y, y = y + y*e.
+template <class P> __device__ __forceinline__ typename P::V vrecip(const typename P::V &x)
+{
+    using T = typename P::T;
+    typename P::V y = vzero<P>();
+    y.c[0] = fpu<T>::div(T(1), x.c[0]);
+    const typename P::V one = vone<P>();
+#pragma unroll 1
+    for (int s = 0; s < P::newton_steps; s++) {
+        typename P::V t = P::mul(x, y);
+        typename P::V e = vsub<P>(one, t);
+        y = P::add(y, P::mul(y, e));
+    }
+    return y;
+}
+
+// Complex product with four real products: re = ar*br - ai*bi, im = ar*bi + ai*br.
+template <class P>
+__device__ __forceinline__ void cmul(const typename P::V &ar, const typename P::V &ai,
+                                     const typename P::V &br, const typename P::V &bi,
+                                     typename P::V &cr, typename P::V &ci)
+{
+    typename P::V t1 = P::mul(ar, br);
+    typename P::V t2 = P::mul(ai, bi);
+    typename P::V t3 = P::mul(ar, bi);
+    typename P::V t4 = P::mul(ai, br);
+    cr = vsub<P>(t1, t2);
+    ci = P::add(t3, t4);
+}
+
+// Complex quotient a / b = (a * conj b) * recip(br^2 + bi^2).
+template <class P>
+__device__ __forceinline__ void cdiv(const typename P::V &ar, const typename P::V &ai,
+                                     const typename P::V &br, const typename P::V &bi,
+                                     typename P::V &cr, typename P::V &ci)
+{
+    typename P::V n2 = P::add(P::mul(br, br), P::mul(bi, bi));
+    typename P::V r = vrecip<P>(n2);
+    typename P::V tr, ti;
+    cmul<P>(ar, ai, br, vneg<P>(bi), tr, ti);
+    cr = P::mul(tr, r);
+    ci = P::mul(ti, r);
+}
+
+}  // namespace mp

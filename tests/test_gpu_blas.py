@@ -1,0 +1,176 @@
+"""GPU parity: elementwise ops, AXPY, dot, GEMV and GEMM through the C ABI
+against the CPU oracle on the same seeded inputs.
+
+Elementwise ops, AXPY and GEMM (sequential k) must match bit for bit; dot and
+GEMV reduce in a tree and must agree with the exact sum within
+(4n + 16) 2^-p sum |x_i y_i|.
+"""
+
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from cases import families
+from exact import SCALE_BITS, mp_ints
+from paper_2603_14926_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+ALL = ["dd", "ddc", "td", "qd", "ds", "tf", "qf"]
+
+
+def dev(x):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def same_bits(a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    if a.shape != b.shape or a.dtype != b.dtype:
+        return False
+    u = np.uint64 if a.dtype == np.float64 else np.uint32
+    return np.array_equal(a.view(u), b.view(u))
+
+
+def pbits(prec):
+    from oracle.mpref import PRECS
+
+    K, dt = PRECS[prec]
+    return K * (53 if dt == np.float64 else 24)
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_elementwise_bit_exact(mp, oracle, prec):
+    K, dt = oracle.PRECS[prec]
+    for name, a, b in families(oracle, prec, n=1537, seed=3):
+        da, db = dev(a), dev(b)
+        assert same_bits(host(mp.add(prec, da, db)), oracle.add(prec, a, b)), name
+        assert same_bits(host(mp.mul(prec, da, db)), oracle.mul(prec, a, b)), name
+    x = inputs.mp_uniform(9, 5003, K, dt) * np.exp2((np.arange(5003) % 61) - 30).astype(dt)
+    assert same_bits(host(mp.recip(prec, dev(x))), oracle.recip(prec, x))
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_axpy_bit_exact(mp, oracle, prec):
+    K, dt = oracle.PRECS[prec]
+    n = 100_003
+    x = inputs.mp_uniform(1, n, K, dt, stream=inputs.STREAM_X)
+    y = inputs.mp_uniform(1, n, K, dt, stream=inputs.STREAM_Y)
+    alpha = inputs.mp_uniform(2, 1, K, dt)[:, 0]
+    dy = dev(y)
+    mp.axpy(prec, alpha, dev(x), dy)
+    assert same_bits(host(dy), oracle.axpy(prec, alpha, x, y))
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd", "qf"])
+@pytest.mark.parametrize("n", [0, 1, 255, 70_001])
+def test_dot_within_bound(mp, oracle, prec, n):
+    K, dt = oracle.PRECS[prec]
+    x = inputs.mp_uniform(4, n, K, dt, stream=inputs.STREAM_X)
+    y = inputs.mp_uniform(4, n, K, dt, stream=inputs.STREAM_Y)
+    g = host(mp.dot(prec, dev(x), dev(y)))
+    if n == 0:
+        assert not np.any(g)
+        return
+    ex = int(mp_ints(x).dot(mp_ints(y)))
+    gi = int(mp_ints(g[:, None])[0])
+    err = float(Fraction(abs(gi * (1 << SCALE_BITS) - ex), 1 << (2 * SCALE_BITS)))
+    mag = float(np.abs(x.astype(np.float64)).sum(0) @ np.abs(y.astype(np.float64)).sum(0))
+    assert err <= (4 * n + 16) * 2.0 ** -pbits(prec) * mag
+    # same bound for the oracle's sequential fold, and the two agree to it
+    o = oracle.dot(prec, x, y)
+    oi = int(mp_ints(o[:, None])[0])
+    assert float(Fraction(abs(oi - gi), 1 << SCALE_BITS)) <= 2 * (4 * n + 16) * 2.0 ** -pbits(prec) * mag
+
+
+def test_dot_workspace_errors(mp):
+    import torch
+
+    x = mp.zeros("qd", 5000)
+    small = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(mp.MPError, match="workspace"):
+        mp.dot("qd", x, x, ws=small)
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "tf"])
+def test_gemv_within_bound(mp, oracle, prec):
+    K, dt = oracle.PRECS[prec]
+    m, n = 37, 1029
+    A = inputs.mp_uniform(5, (m, n), K, dt)
+    x = inputs.mp_uniform(6, n, K, dt, stream=inputs.STREAM_X)
+    g = host(mp.gemv(prec, dev(A), dev(x)))
+    Ai, xi = mp_ints(A), mp_ints(x)
+    absA = np.abs(A.astype(np.float64)).sum(0)
+    absx = np.abs(x.astype(np.float64)).sum(0)
+    for i in range(m):
+        ex = int(Ai[i].dot(xi))
+        gi = int(mp_ints(g[:, i:i + 1])[0])
+        err = float(Fraction(abs(gi * (1 << SCALE_BITS) - ex), 1 << (2 * SCALE_BITS)))
+        assert err <= (4 * n + 16) * 2.0 ** -pbits(prec) * float(absA[i] @ absx)
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_gemm_config0_bit_exact(mp, oracle, prec):
+    """n = 64, seed 0 (the oracle's exact-rational pin uses the same inputs)."""
+    K, dt = oracle.PRECS[prec]
+    n = 64
+    A = inputs.mp_uniform(0, (n, n), K, dt, stream=inputs.STREAM_A)
+    B = inputs.mp_uniform(0, (n, n), K, dt, stream=inputs.STREAM_B)
+    want = oracle.gemm(prec, A, B)
+    for cfg in range(mp.gemm_num_configs(prec)):
+        assert same_bits(host(mp.gemm(prec, dev(A), dev(B), config=cfg)), want), cfg
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "qd", "qf", "tf"])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_ragged_transposed_bit_exact(mp, oracle, prec, opA, opB):
+    """Ragged sizes spanning several tiles, every operand mode, every configuration."""
+    K, dt = oracle.PRECS[prec]
+    m, n, k = 70, 45, 133
+    A = inputs.mp_uniform(7, (k, m) if opA else (m, k), K, dt)
+    B = inputs.mp_uniform(8, (n, k) if opB else (k, n), K, dt)
+    want = oracle.gemm(prec, A, B, opA, opB)
+    for cfg in range(mp.gemm_num_configs(prec)):
+        got = host(mp.gemm(prec, dev(A), dev(B), opA, opB, config=cfg))
+        assert same_bits(got, want), (cfg, opA, opB)
+
+
+def test_gemm_degenerate_sizes(mp, oracle):
+    import torch
+
+    prec = "qd"
+    A = mp.zeros(prec, 5, 0)
+    B = mp.zeros(prec, 0, 7)
+    C = torch.full((4, 5, 7), 3.0, dtype=torch.float64, device="cuda")
+    mp.gemm(prec, A, B, out=C)
+    assert not torch.any(C)
+    assert mp.gemm(prec, mp.zeros(prec, 0, 3), mp.zeros(prec, 3, 4)).shape == (4, 0, 4)
+    with pytest.raises(mp.MPError, match="invalid"):
+        mp.gemm(prec, mp.zeros(prec, 3, 3), mp.zeros(prec, 3, 3), opA=2)
+
+
+@pytest.mark.parametrize("prec,n", [("qd", 2048), ("dd", 4096)])
+def test_gemm_full_size_sampled(mp, oracle, prec, n):
+    """The benchmark's size and launch configuration: 48 sampled entries recomputed
+    by the oracle one by one must match bit for bit."""
+    K, dt = oracle.PRECS[prec]
+    A = inputs.mp_uniform(2, (n, n), K, dt, stream=inputs.STREAM_A)
+    B = inputs.mp_uniform(2, (n, n), K, dt, stream=inputs.STREAM_B)
+    C = host(mp.gemm(prec, dev(A), dev(B)))
+    rng = np.random.default_rng(0)
+    rows = np.concatenate([[0, n - 1], rng.integers(0, n, 46)])
+    cols = np.concatenate([[n - 1, 0], rng.integers(0, n, 46)])
+    for i, j in zip(rows, cols):
+        want = oracle.gemm(prec, A[:, i:i + 1, :], B[:, :, j:j + 1])[:, 0, 0]
+        assert same_bits(C[:, i, j], want), (i, j)
+
+
+def test_peak_microbenchmark_runs(mp):
+    rate, ms = mp.peak(0, iters=256)
+    assert rate > 0 and ms > 0

@@ -15,6 +15,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+from cases import families
 from exact import mp_value, mp_values, rel_err, to_mp
 from paper_2603_14926_gb300 import inputs
 
@@ -109,32 +110,6 @@ def test_op_counts_double_word(oracle):
 # ---------------------------------------------------------------------------
 # Inputs: random nonoverlapping numbers, exponent gaps, near-cancellation, zeros
 # ---------------------------------------------------------------------------
-
-def families(oracle, prec, n=600, seed=0):
-    K, dt = oracle.PRECS[prec]
-    f32 = dt == np.float32
-    rng = np.random.default_rng(100 + seed)
-    out = []
-    a = inputs.mp_uniform(seed, n, K, dt, stream=41)
-    b = inputs.mp_uniform(seed, n, K, dt, stream=42)
-    out.append(("random", a, b))
-    gap = rng.integers(-12, 13, n) if f32 else rng.integers(-60, 61, n)
-    out.append(("exponent-gap", a, (b * np.exp2(gap)).astype(dt)))
-    # near-cancellation: b = -(a + eps) re-expanded exactly into K components
-    m = n // 3
-    eps = inputs.mp_uniform(seed, m, K, dt, stream=43)
-    sh = rng.integers(5, 40 if f32 else 150, m)
-    bb = np.zeros((K, m), dtype=dt)
-    for i in range(m):
-        q = -(mp_value(a[:, i]) + mp_value(eps[:, i]) * Fraction(2) ** int(-sh[i]))
-        bb[:, i] = to_mp(q, K, dt)
-    out.append(("cancellation", a[:, :m].copy(), bb))
-    z = b.copy()
-    z[1:, : n // 4] = 0
-    z[2:, n // 4: n // 2] = 0
-    out.append(("zero-components", a, z))
-    return out
-
 
 @pytest.mark.parametrize("prec", BF_PRECS)
 @pytest.mark.parametrize("op", ["add", "mul"])
