@@ -156,19 +156,23 @@ const char *mp_version(void);
     mp_status mp_polyeval_##P(int64_t npoly, const int64_t *coef_off, const T *coef,         \
                               int64_t pcoef, int64_t npts, const T *x_re, const T *x_im,     \
                               int64_t px, T *y_re, T *y_im, int64_t py, mp_stream stream);   \
+    size_t mp_polyeval_backward_workspace_##P(int64_t npoly, int64_t npts);                 \
     mp_status mp_polyeval_backward_##P(int64_t npoly, const int64_t *coef_off, const T *coef,\
                                        int64_t pcoef, int64_t npts, const T *x, int64_t px,  \
                                        const T *dy, int64_t pdy, T *dcoef, int64_t pdc,      \
-                                       T *dx, int64_t pdx, mp_stream stream);
+                                       T *dx, int64_t pdx, void *ws, size_t ws_bytes,        \
+                                       mp_stream stream);
 
 /* POLYEVAL_BACKWARD: adjoint of the real-argument evaluation for a given dy:   */
 /*   dx_{b,m}    = mul(dy_{b,m}, p_b'(x_{b,m})), p' by the simultaneous Horner   */
-/*                 recurrence d = add(mul(d,x), h); h = add(mul(h,x), a_i)       */
-/*                 (bit-identical to the oracle);                                */
-/*   dcoef_{b,i} = sum over m of w_{b,m,i}, w_0 = dy, w_{i+1} = mul(w_i, x): the */
-/*                 reverse sweep of Horner's recurrence, summed over the points  */
-/*                 by a block tree (within (4(npts+i)+16) 2^-p sum |dy x^i| of   */
-/*                 the exact sum).  Either output may be NULL.                   */
+/*                 recurrence d = add(mul(d,x), h); h = add(mul(h,x), a_i);      */
+/*   dcoef_{b,i} = sum over m ascending of w_{b,m,i} (fold from 0 with add),     */
+/*                 w_0 = dy, w_{i+1} = mul(w_i, x): the reverse sweep of Horner's*/
+/*                 recurrence h_i = h_{i+1} x + a_i.                             */
+/* Both are bit-identical to the CPU oracle.  Either output may be NULL.        */
+/* ws: DEVICE workspace of mp_polyeval_backward_workspace_P(npoly, npts) bytes   */
+/* (the running powers between blocks of 32 coefficients; needed only when      */
+/* dcoef != NULL, contents need no initialisation).                             */
 
 /* ------------------------------------------------------------------------ */
 /* POLY_FROM_ROOTS: coefficients of prod (x - r) (the root-solving workload): */
@@ -178,7 +182,8 @@ const char *mp_version(void);
 /* neg(mul(r, p_i))); each pair: x^2 + B x + C, B = -2 re, C = add(mul(re,re),*/
 /* mul(im,im)), p'_i = add(add(p_{i-2}, mul(B, p_{i-1})), mul(C, p_i));     */
 /* finally a_i = mul(a_i, (1, delta_i)) for i < n.  rootdata/delta are      */
-/* indexed from coef_off[b] - b.  Bit-identical to the CPU oracle.          */
+/* indexed from coef_off[b] - b.  max_degree: host bound on every degree   */
+/* (polynomials above it are left unwritten).  Bit-identical to the oracle. */
 /* ------------------------------------------------------------------------ */
 
 /* ------------------------------------------------------------------------ */
@@ -230,7 +235,8 @@ typedef struct {
 #define MPGPU_DECL_ROOTS(P)                                                                 \
     mp_status mp_poly_from_roots_##P(int64_t npoly, const int64_t *coef_off,                \
                                      const double *rootdata, const double *delta,            \
-                                     double *coef, int64_t pcoef, mp_stream stream);         \
+                                     int32_t max_degree, double *coef, int64_t pcoef,        \
+                                     mp_stream stream);                                      \
     mp_status mp_roots_init_##P(int64_t npoly, const int64_t *coef_off, const double *coef,  \
                                 int64_t pcoef, double radius, int32_t max_degree, double *z, \
                                 int64_t pz, mp_stream stream);                               \

@@ -72,7 +72,7 @@ def _declare(L):
                         _i64, _i64, _int, _vp],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
-                                  _vp, _i64, _vp],
+                                  _vp, _i64, _vp, ctypes.c_size_t, _vp],
         }
         for name, args in sigs.items():
             f = getattr(L, f"mp_{name}_{p}", None)
@@ -82,6 +82,8 @@ def _declare(L):
             f.restype = _int
         getattr(L, f"mp_dot_workspace_{p}").argtypes = [_i64]
         getattr(L, f"mp_dot_workspace_{p}").restype = ctypes.c_size_t
+        getattr(L, f"mp_polyeval_backward_workspace_{p}").argtypes = [_i64, _i64]
+        getattr(L, f"mp_polyeval_backward_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
         getattr(L, f"mp_gemm_config_name_{p}").argtypes = [_int]
         getattr(L, f"mp_gemm_config_name_{p}").restype = ctypes.c_char_p
@@ -89,7 +91,7 @@ def _declare(L):
         f = getattr(L, f"mp_poly_from_roots_{p}", None)
         if f is None:
             continue
-        f.argtypes = [_i64, _vp, _vp, _vp, _vp, _i64, _vp]
+        f.argtypes = [_i64, _vp, _vp, _vp, _i32, _vp, _i64, _vp]
         f.restype = _int
         f = getattr(L, f"mp_roots_init_{p}")
         f.argtypes = [_i64, _vp, _vp, _i64, _dbl, _i32, _vp, _i64, _vp]
@@ -308,27 +310,36 @@ def polyeval(prec, coef_off, coef, npts, x_re, x_im=None):
     return (y_re, y_im) if x_im is not None else y_re
 
 
-def polyeval_backward(prec, coef_off, coef, npts, x, dy, want_dcoef=True, want_dx=True):
+def polyeval_backward_workspace(prec, npoly, npts):
+    return int(getattr(lib(), f"mp_polyeval_backward_workspace_{prec}")(npoly, npts))
+
+
+def polyeval_backward(prec, coef_off, coef, npts, x, dy, want_dcoef=True, want_dx=True, ws=None):
+    """Adjoint of real-argument polyeval: returns (dcoef, dx) (None where not wanted)."""
+    t = _torch()
     _check(prec, coef, "coef", 2)
     _check(prec, x, "x", 2)
     _check(prec, dy, "dy", 2)
     npoly = coef_off.numel() - 1
     dcoef = empty(prec, coef.shape[1], device=coef.device) if want_dcoef else None
     dx = empty(prec, x.shape[1], device=coef.device) if want_dx else None
+    nb = polyeval_backward_workspace(prec, npoly, npts) if want_dcoef else 0
+    if ws is None and nb:
+        ws = t.empty(nb, dtype=t.uint8, device=coef.device)
     _call(f"mp_polyeval_backward_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), npts,
           _ptr(x), _ps(x), _ptr(dy), _ps(dy), _ptr(dcoef), _ps(dcoef) if dcoef is not None else 0,
-          _ptr(dx), _ps(dx) if dx is not None else 0, _stream())
+          _ptr(dx), _ps(dx) if dx is not None else 0, _ptr(ws),
+          ws.numel() * ws.element_size() if ws is not None else 0, _stream())
     return dcoef, dx
 
 
-def poly_from_roots(prec, coef_off, rootdata, delta):
-    """Coefficients of the root-solving workload (see inputs.DKProblem)."""
-    K = PRECS[prec][0]
-    npoly = coef_off.numel() - 1
-    total = int(coef_off[-1].item()) if coef_off.is_cuda else int(coef_off[-1])
+def poly_from_roots(prec, coef_off, rootdata, delta, max_degree, total):
+    """Coefficients (K, total) of the root-solving workload (see inputs.DKProblem);
+    coef_off, rootdata and delta are CUDA tensors, max_degree and total host ints."""
     coef = empty(prec, total, device=rootdata.device)
+    npoly = coef_off.numel() - 1
     _call(f"mp_poly_from_roots_{prec}", npoly, _ptr(coef_off), _ptr(rootdata), _ptr(delta),
-          _ptr(coef), _ps(coef), _stream())
+          int(max_degree), _ptr(coef), _ps(coef), _stream())
     return coef
 
 

@@ -1,0 +1,358 @@
+// k_poly.cu -- polynomial evaluation (Section 4.1), its adjoint, and the
+// construction of polynomials from their roots, in multicomponent arithmetic.
+//
+// Evaluation: one thread per (polynomial, point), Horner's rule with the
+// coefficients read as warp-uniform broadcasts.  Real arguments cost one
+// multiply and one add per coefficient (209 FP64 instructions in QD), complex
+// arguments four multiplies and three adds.
+//
+// Adjoint, dy -> (dcoef, dx):
+//   dx: one thread per point, simultaneous Horner recurrence for p'.
+//   dcoef_i = sum over points m (ascending) of dy_m x_m^i.  One warp per
+//   polynomial sweeps blocks of 32 coefficients as a wavefront: lane L owns
+//   coefficient 32j+L and at step s handles point m = s - L, receiving
+//   dy_m x_m^(i-1) * x_m from lane L-1 through a register shuffle.  Each
+//   coefficient is therefore folded over the points in ascending order with the
+//   powers formed by repeated multiplication -- the oracle's order, so the
+//   result is bit-identical -- while all 32 lanes do useful work in all but 31
+//   of npts + 31 steps.  Lane 31 hands the running powers of the next block
+//   (dy_m x_m^(32(j+1))) to the next sweep through a per-point workspace.
+//
+// Polynomials from roots: one block per polynomial, the coefficient vector in
+// shared memory, one factor (x - r) or (x^2 + Bx + C) per synchronised stage,
+// all coefficients of a stage in parallel.
+#include <cuda_runtime.h>
+
+#include "mp_arith.cuh"
+#include "mp_common.cuh"
+
+namespace mp {
+
+// ---------------------------------------------------------------------------
+// Evaluation
+// ---------------------------------------------------------------------------
+
+template <class P, bool CPLX>
+__global__ void __launch_bounds__(256) k_polyeval(int64_t npoly, const int64_t *__restrict__ coef_off,
+                                                  const typename P::T *__restrict__ coef, int64_t pc,
+                                                  int64_t npts, const typename P::T *__restrict__ xr,
+                                                  const typename P::T *__restrict__ xi, int64_t px,
+                                                  typename P::T *__restrict__ yr,
+                                                  typename P::T *__restrict__ yi, int64_t py)
+{
+    using V = typename P::V;
+    const int64_t total = npoly * npts;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const int64_t b = idx / npts;
+        const int64_t off = coef_off[b];
+        const int64_t n = coef_off[b + 1] - off - 1;
+        const typename P::T *cb = coef + off;
+        if (n < 0) {
+            vstore<P>(yr, py, idx, vzero<P>());
+            if (CPLX) vstore<P>(yi, py, idx, vzero<P>());
+            continue;
+        }
+        const V zr = vload<P>(xr, px, idx);
+        V hr = vload<P>(cb, pc, n);
+        if (!CPLX) {
+            for (int64_t i = n - 1; i >= 0; i--) hr = P::add(P::mul(hr, zr), vload<P>(cb, pc, i));
+            vstore<P>(yr, py, idx, hr);
+        } else {
+            const V zi = vload<P>(xi, px, idx);
+            V hi = vzero<P>();
+            for (int64_t i = n - 1; i >= 0; i--) {
+                V t1 = P::mul(hr, zr);
+                V t2 = P::mul(hi, zi);
+                t1 = vsub<P>(t1, t2);
+                t1 = P::add(t1, vload<P>(cb, pc, i));
+                V t3 = P::mul(hr, zi);
+                V t4 = P::mul(hi, zr);
+                hi = P::add(t3, t4);
+                hr = t1;
+            }
+            vstore<P>(yr, py, idx, hr);
+            vstore<P>(yi, py, idx, hi);
+        }
+    }
+}
+
+template <class P>
+static mp_status polyeval_launch(int64_t npoly, const int64_t *coef_off, const typename P::T *coef,
+                                 int64_t pc, int64_t npts, const typename P::T *xr,
+                                 const typename P::T *xi, int64_t px, typename P::T *yr,
+                                 typename P::T *yi, int64_t py, mp_stream s)
+{
+    if (npoly < 0 || npts < 0) return MP_EINVAL;
+    const int64_t total = npoly * npts;
+    if (total == 0) return MP_OK;
+    if (coef_off == nullptr || coef == nullptr || pc < 1 || !planes_ok(xr, total, px) ||
+        !planes_ok(yr, total, py))
+        return MP_EINVAL;
+    if ((xi == nullptr) != (yi == nullptr)) return MP_EINVAL;
+    const unsigned g = grid_for(total, 256, 8);
+    if (xi)
+        k_polyeval<P, true><<<g, 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, xr, xi, px, yr,
+                                                         yi, py);
+    else
+        k_polyeval<P, false><<<g, 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, xr, xi, px, yr,
+                                                          yi, py);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+
+template <class P>
+__global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *__restrict__ coef_off,
+                                                 const typename P::T *__restrict__ coef, int64_t pc,
+                                                 int64_t npts, const typename P::T *__restrict__ x,
+                                                 int64_t px, const typename P::T *__restrict__ dy,
+                                                 int64_t pdy, typename P::T *__restrict__ dx, int64_t pdx)
+{
+    using V = typename P::V;
+    const int64_t total = npoly * npts;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const int64_t b = idx / npts;
+        const int64_t off = coef_off[b];
+        const int64_t n = coef_off[b + 1] - off - 1;
+        if (n < 0) {
+            vstore<P>(dx, pdx, idx, vzero<P>());
+            continue;
+        }
+        const typename P::T *cb = coef + off;
+        const V xm = vload<P>(x, px, idx);
+        V h = vload<P>(cb, pc, n);
+        V d = vzero<P>();
+        for (int64_t i = n - 1; i >= 0; i--) {
+            d = P::add(P::mul(d, xm), h);
+            h = P::add(P::mul(h, xm), vload<P>(cb, pc, i));
+        }
+        vstore<P>(dx, pdx, idx, P::mul(vload<P>(dy, pdy, idx), d));
+    }
+}
+
+constexpr int DCOEF_WARPS = 4;
+
+template <class P>
+__global__ void __launch_bounds__(32 * DCOEF_WARPS)
+    k_poly_dcoef(int64_t npoly, const int64_t *__restrict__ coef_off, int64_t npts,
+                 const typename P::T *__restrict__ x, int64_t px, const typename P::T *__restrict__ dy,
+                 int64_t pdy, typename P::T *__restrict__ dcoef, int64_t pdc, typename P::T *__restrict__ wbuf,
+                 int64_t pw)
+{
+    using V = typename P::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * DCOEF_WARPS + (threadIdx.x >> 5);
+    if (b >= npoly) return;  // whole warp
+    const int64_t off = coef_off[b];
+    const int64_t n = coef_off[b + 1] - off - 1;
+    if (n < 0) return;
+    const int64_t base = b * npts;  // this polynomial's points
+    for (int64_t j0 = 0; j0 <= n; j0 += 32) {
+        const int64_t i = j0 + lane;
+        V S = vzero<P>();
+        V win = vzero<P>();
+        for (int64_t s = 0; s < npts + 31; s++) {
+            const int64_t m = s - lane;
+            const bool act = m >= 0 && m < npts && i <= n;
+            V w = win;
+            if (lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
+            V wout = vzero<P>();
+            if (act) {
+                S = P::add(S, w);
+                if (i < n) wout = P::mul(w, vload<P>(x, px, base + m));
+            }
+            if (lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout);
+#pragma unroll
+            for (int c = 0; c < P::K; c++) win.c[c] = __shfl_up_sync(0xffffffffu, wout.c[c], 1);
+        }
+        if (i <= n) vstore<P>(dcoef, pdc, off + i, S);
+        __syncwarp();
+    }
+}
+
+template <class P> static size_t backward_ws(int64_t npoly, int64_t npts)
+{
+    if (npoly <= 0 || npts <= 0) return 0;
+    return (size_t)npoly * (size_t)npts * P::K * sizeof(typename P::T);
+}
+
+template <class P>
+static mp_status polyeval_backward_launch(int64_t npoly, const int64_t *coef_off, const typename P::T *coef,
+                                          int64_t pc, int64_t npts, const typename P::T *x, int64_t px,
+                                          const typename P::T *dy, int64_t pdy, typename P::T *dcoef,
+                                          int64_t pdc, typename P::T *dx, int64_t pdx, void *ws,
+                                          size_t ws_bytes, mp_stream s)
+{
+    if (npoly < 0 || npts < 0) return MP_EINVAL;
+    const int64_t total = npoly * npts;
+    if (npoly == 0) return MP_OK;
+    if (coef_off == nullptr || coef == nullptr || pc < 1) return MP_EINVAL;
+    if (total > 0 && (!planes_ok(x, total, px) || !planes_ok(dy, total, pdy))) return MP_EINVAL;
+    if (dx && total > 0) {
+        if (pdx < total) return MP_EINVAL;
+        k_poly_dx<P><<<grid_for(total, 256, 8), 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, x,
+                                                                         px, dy, pdy, dx, pdx);
+        mp_status st = launch_status();
+        if (st != MP_OK) return st;
+    }
+    if (dcoef) {
+        if (pdc < 1) return MP_EINVAL;
+        if (total > 0 && (ws == nullptr || ws_bytes < backward_ws<P>(npoly, npts))) return MP_ENOMEM;
+        const int64_t blocks = (npoly + DCOEF_WARPS - 1) / DCOEF_WARPS;
+        k_poly_dcoef<P><<<(unsigned)blocks, 32 * DCOEF_WARPS, 0, as_stream(s)>>>(
+            npoly, coef_off, npts, x, px, dy, pdy, dcoef, pdc, static_cast<typename P::T *>(ws), total);
+        return launch_status();
+    }
+    return MP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Polynomials from roots
+// ---------------------------------------------------------------------------
+
+constexpr int BUILD_THREADS = 128;
+
+template <class P>
+__global__ void __launch_bounds__(BUILD_THREADS)
+    k_poly_from_roots(int64_t npoly, const int64_t *__restrict__ coef_off, const double *__restrict__ rootdata,
+                      const double *__restrict__ delta, int32_t max_degree, typename P::T *__restrict__ coef,
+                      int64_t pc)
+{
+    using T = typename P::T;
+    using V = typename P::V;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t b = blockIdx.x;
+    const int64_t off = coef_off[b];
+    const int64_t n = coef_off[b + 1] - off - 1;
+    if (n < 0 || n > max_degree) return;
+    const int64_t cap = (int64_t)max_degree + 1;  // plane stride of the work vectors
+    T *p = reinterpret_cast<T *>(smem_raw);
+    T *q = p + P::K * cap;
+    T *cq = q + P::K * cap;  // C of each quadratic factor, plane stride cap/2+1
+    const int64_t pq = cap / 2 + 1;
+    const double *rd = rootdata + (off - b);
+    const double *dl = delta + (off - b);
+    const int64_t npair = n / 2;
+    for (int64_t k = threadIdx.x; k < npair; k += blockDim.x) {
+        V re = vzero<P>(), im = vzero<P>();
+        re.c[0] = rd[2 * k];
+        im.c[0] = rd[2 * k + 1];
+        vstore<P>(cq, pq, k, P::add(P::mul(re, re), P::mul(im, im)));
+    }
+    if (threadIdx.x == 0) vstore<P>(p, cap, 0, vone<P>());
+    __syncthreads();
+    int64_t d = 0;
+    if (n % 2) {
+        V r = vzero<P>();
+        r.c[0] = rd[n - 1];
+        for (int64_t i = threadIdx.x; i <= d + 1; i += blockDim.x) {
+            V acc = i >= 1 ? vload<P>(p, cap, i - 1) : vzero<P>();
+            if (i <= d) acc = P::add(acc, vneg<P>(P::mul(r, vload<P>(p, cap, i))));
+            vstore<P>(q, cap, i, acc);
+        }
+        __syncthreads();
+        T *t = p; p = q; q = t;
+        d += 1;
+    }
+    for (int64_t k = 0; k < npair; k++) {
+        V B = vzero<P>();
+        B.c[0] = -2.0 * rd[2 * k];  // power-of-two scale: exact
+        const V C = vload<P>(cq, pq, k);
+        for (int64_t i = threadIdx.x; i <= d + 2; i += blockDim.x) {
+            V acc = i >= 2 ? vload<P>(p, cap, i - 2) : vzero<P>();
+            if (i >= 1 && i - 1 <= d) acc = P::add(acc, P::mul(B, vload<P>(p, cap, i - 1)));
+            if (i <= d) acc = P::add(acc, P::mul(C, vload<P>(p, cap, i)));
+            vstore<P>(q, cap, i, acc);
+        }
+        __syncthreads();
+        T *t = p; p = q; q = t;
+        d += 2;
+    }
+    for (int64_t i = threadIdx.x; i <= n; i += blockDim.x) {
+        V a = vload<P>(p, cap, i);
+        if (i < n) {
+            V f = vone<P>();
+            f.c[1] = dl[i];
+            a = P::mul(a, f);
+        }
+        vstore<P>(coef + off, pc, i, a);
+    }
+}
+
+constexpr int32_t BUILD_MAX_DEGREE = 2048;
+
+template <class P>
+static mp_status poly_from_roots_launch(int64_t npoly, const int64_t *coef_off, const double *rootdata,
+                                        const double *delta, int32_t max_degree, typename P::T *coef,
+                                        int64_t pc, mp_stream s)
+{
+    if (npoly < 0 || max_degree < 0 || max_degree > BUILD_MAX_DEGREE) return MP_EINVAL;
+    if (npoly == 0) return MP_OK;
+    if (coef_off == nullptr || coef == nullptr || pc < 1) return MP_EINVAL;
+    if (max_degree > 0 && (rootdata == nullptr || delta == nullptr)) return MP_EINVAL;
+    const int64_t cap = (int64_t)max_degree + 1;
+    const size_t smem = (size_t)P::K * sizeof(typename P::T) * (2 * cap + cap / 2 + 1);
+    if (npoly > 0x7fffffff) return MP_EINVAL;
+    cudaError_t e = cudaFuncSetAttribute(k_poly_from_roots<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    k_poly_from_roots<P><<<(unsigned)npoly, BUILD_THREADS, smem, as_stream(s)>>>(npoly, coef_off, rootdata,
+                                                                                  delta, max_degree, coef, pc);
+    return launch_status();
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+#define MP_EXPORT_POLY(S, PT)                                                                       \
+    mp_status mp_polyeval_##S(int64_t npoly, const int64_t *coef_off, const PT::T *coef,           \
+                              int64_t pcoef, int64_t npts, const PT::T *x_re, const PT::T *x_im,    \
+                              int64_t px, PT::T *y_re, PT::T *y_im, int64_t py, mp_stream s)       \
+    {                                                                                               \
+        return polyeval_launch<PT>(npoly, coef_off, coef, pcoef, npts, x_re, x_im, px, y_re, y_im, \
+                                   py, s);                                                          \
+    }                                                                                               \
+    size_t mp_polyeval_backward_workspace_##S(int64_t npoly, int64_t npts)                          \
+    {                                                                                               \
+        return backward_ws<PT>(npoly, npts);                                                        \
+    }                                                                                               \
+    mp_status mp_polyeval_backward_##S(int64_t npoly, const int64_t *coef_off, const PT::T *coef,  \
+                                       int64_t pcoef, int64_t npts, const PT::T *x, int64_t px,     \
+                                       const PT::T *dy, int64_t pdy, PT::T *dcoef, int64_t pdc,     \
+                                       PT::T *dx, int64_t pdx, void *ws, size_t ws_bytes,           \
+                                       mp_stream s)                                                 \
+    {                                                                                               \
+        return polyeval_backward_launch<PT>(npoly, coef_off, coef, pcoef, npts, x, px, dy, pdy,     \
+                                            dcoef, pdc, dx, pdx, ws, ws_bytes, s);                  \
+    }
+
+MP_EXPORT_POLY(dd, P_dd)
+MP_EXPORT_POLY(ddc, P_ddc)
+MP_EXPORT_POLY(td, P_td)
+MP_EXPORT_POLY(qd, P_qd)
+MP_EXPORT_POLY(ds, P_ds)
+MP_EXPORT_POLY(tf, P_tf)
+MP_EXPORT_POLY(qf, P_qf)
+
+#define MP_EXPORT_BUILD(S, PT)                                                                      \
+    mp_status mp_poly_from_roots_##S(int64_t npoly, const int64_t *coef_off, const double *rootdata, \
+                                     const double *delta, int32_t max_degree, double *coef,          \
+                                     int64_t pcoef, mp_stream s)                                     \
+    {                                                                                               \
+        return poly_from_roots_launch<PT>(npoly, coef_off, rootdata, delta, max_degree, coef, pcoef, \
+                                          s);                                                       \
+    }
+
+MP_EXPORT_BUILD(dd, P_dd)
+MP_EXPORT_BUILD(ddc, P_ddc)
+MP_EXPORT_BUILD(td, P_td)
+MP_EXPORT_BUILD(qd, P_qd)
+
+}  // extern "C"

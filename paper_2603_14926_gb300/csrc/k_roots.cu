@@ -1,0 +1,607 @@
+// k_roots.cu -- batched Durand-Kerner all-roots solver (Section 4.2, Eq. 4)
+// with Aberth starting values (Eq. 5), in complex multicomponent arithmetic.
+//
+// One block solves one polynomial.  Its monic coefficients and the current
+// Jacobi iterate live in shared memory; the next iterate is written to the
+// polynomial's slice of the caller's `roots` output (global memory this block
+// alone owns) and copied back after the sweep's barrier, which halves the shared
+// memory per block (four 128-thread blocks per SM at degree 500 in QD).  Thread
+// t owns roots t, t + blockDim, ...  A sweep computes, for every owned root i,
+//   q(z_i) by complex Horner over the coefficients (shared-memory broadcasts),
+//   prod_{j != i} (z_i - z_j) over the current iterate (broadcasts),
+//   w_i = q / prod, z_i' = z_i - w_i,
+// then the block reduces delta = max |w_i| and zmax = max |z_i'| (binary64
+// maxima on leading components: exact, so the reduction order cannot change
+// them) and every thread takes the same stopping decision.  Per root and sweep
+// this is n (4 mul + 3 add) + (n - 1) (4 mul + 4 add) multicomponent operations:
+// about 1569 n FP64 instructions in QD, all on the FP64 pipe.
+//
+// Batching: mode 0 is one persistent launch: SMs x blocks_per_sm blocks pop
+// polynomial indices from an atomic counter in the workspace (optionally in
+// descending degree order, computed on the device), so uneven degrees balance
+// across the GPU without host involvement; the launch is capturable in a CUDA
+// graph.  Mode 1 is the plain per-polynomial launch loop (one single-block
+// launch per polynomial) running the same device code, hence the same bits.
+//
+// Every step restates the operation order of the CPU oracle; see mpgpu.h for
+// the stopping rule, the extended exponent of q and of the product, and the
+// starting values.  There are no inter-block waits; the optional watchdog is a
+// per-polynomial clock64 budget that ends the iteration with status 3.
+#include <cuda_runtime.h>
+
+#include "mp_arith.cuh"
+#include "mp_common.cuh"
+
+namespace mp {
+
+enum { DK_CAP = 0, DK_CONVERGED = 1, DK_STAGNATED = 2, DK_TIMEOUT = 3, DK_BREAKDOWN = 4 };
+
+// ---------------------------------------------------------------------------
+// Binary64 helpers with fixed operation sequences (shared with nothing: the
+// CPU oracle restates the same definitions independently).
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double pow2(int e)  // exact 2^e for -1022 <= e <= 1023
+{
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__device__ __forceinline__ int bexp(double x)  // biased exponent field
+{
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// x = mant * 2^e with mant in [0.5, 1), for finite x > 0 (C frexp semantics).
+__device__ __forceinline__ double frexp_pos(double x, int &e)
+{
+    int adj = 0;
+    if (bexp(x) == 0) {  // subnormal: scale into the normal range first (exact)
+        x = __dmul_rn(x, pow2(54));
+        adj = -54;
+    }
+    long long u = __double_as_longlong(x);
+    e = (int)((u >> 52) & 0x7ff) - 1022 + adj;
+    u = (u & ~(0x7ffLL << 52)) | (1022LL << 52);
+    return __longlong_as_double(u);
+}
+
+// x * 2^q correctly rounded (C ldexp), for x in [1, 2) and any q.
+__device__ __forceinline__ double ldexp_pos(double x, long long q)
+{
+    if (q > 1023) return __dmul_rn(__dmul_rn(x, pow2(1023)), pow2((int)(q - 1023 > 1023 ? 1023 : q - 1023)));
+    if (q >= -1022) return __dmul_rn(x, pow2((int)q));
+    long long q2 = q + 54;
+    if (q2 < -1022) return 0.0 * x;
+    return __dmul_rn(__dmul_rn(x, pow2((int)q2)), pow2(-54));
+}
+
+__constant__ double kPI = 0x1.921fb54442d18p+1;
+__constant__ double kLN2 = 0x1.62e42fefa39efp-1;
+
+// cos and sin of theta in [0, 2 pi): Taylor series of cos/sin(theta - pi), 18 terms.
+__device__ void dk_cos_sin(double theta, double &c, double &s)
+{
+    const double phi = __dsub_rn(theta, kPI);
+    const double mx2 = -__dmul_rn(phi, phi);
+    double ct = 1.0, cs = 1.0, st = phi, ss = phi;
+    for (int k = 1; k <= 17; k++) {
+        ct = __ddiv_rn(__dmul_rn(ct, mx2), (double)((2 * k - 1) * (2 * k)));
+        st = __ddiv_rn(__dmul_rn(st, mx2), (double)((2 * k) * (2 * k + 1)));
+        cs = __dadd_rn(cs, ct);
+        ss = __dadd_rn(ss, st);
+    }
+    c = -cs;
+    s = -ss;
+}
+
+// log2 f, f in [1, 2): 2 atanh((f-1)/(f+1)) / ln 2, series to 18 terms.
+__device__ double dk_log2_1to2(double f)
+{
+    const double u = __ddiv_rn(__dsub_rn(f, 1.0), __dadd_rn(f, 1.0));
+    const double u2 = __dmul_rn(u, u);
+    double pw = u, sum = u;
+    for (int k = 1; k <= 17; k++) {
+        pw = __dmul_rn(pw, u2);
+        sum = __dadd_rn(sum, __ddiv_rn(pw, (double)(2 * k + 1)));
+    }
+    return __ddiv_rn(__dmul_rn(2.0, sum), kLN2);
+}
+
+// 2^t, t in [0, 1): Taylor series of exp(t ln 2), 21 terms.
+__device__ double dk_exp2_0to1(double t)
+{
+    const double y = __dmul_rn(t, kLN2);
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k <= 20; k++) {
+        term = __ddiv_rn(__dmul_rn(term, y), (double)k);
+        sum = __dadd_rn(sum, term);
+    }
+    return sum;
+}
+
+// v^(1/m) for v > 0, m >= 1; NaN for a non-finite v (as frexp/ldexp propagate it),
+// which the radius maximum then ignores.
+__device__ double dk_nthroot(double v, long long m)
+{
+    if (!(v < __longlong_as_double(0x7ff0000000000000LL))) return __longlong_as_double(0x7ff8000000000000LL);
+    int e;
+    const double mant = frexp_pos(v, e);
+    const double f = __dmul_rn(2.0, mant);
+    const long long ee = (long long)e - 1;
+    const long long q = ee >= 0 ? ee / m : -((-ee + m - 1) / m);
+    const long long s = ee - q * m;
+    const double t = __ddiv_rn(__dadd_rn((double)s, dk_log2_1to2(f)), (double)m);
+    return ldexp_pos(dk_exp2_0to1(t), q);
+}
+
+// x := x * 2^s componentwise, |s| <= 1000.
+template <class P> __device__ __forceinline__ void vscale(typename P::V &x, int s)
+{
+    const double f = pow2(s);
+#pragma unroll
+    for (int c = 0; c < P::K; c++) x.c[c] = __dmul_rn(x.c[c], f);
+}
+
+template <class P> __device__ __forceinline__ void vscale_big(typename P::V &x, long long d)
+{
+    while (d > 512) {
+        vscale<P>(x, 512);
+        d -= 512;
+    }
+    while (d < -512) {
+        vscale<P>(x, -512);
+        d += 512;
+    }
+    if (d != 0) vscale<P>(x, (int)d);
+}
+
+constexpr int DK_RESCALE = 256;
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one polynomial's solve
+// ---------------------------------------------------------------------------
+
+struct DKShared {
+    double delta, zmax, center, radius;
+    int bad, stop, nnz, pad;
+    double red[2][32];
+    int redi[32];
+};
+
+template <class P> struct DKArgs {
+    int64_t npoly;
+    const int64_t *coef_off;
+    const double *coef;
+    int64_t pcoef;
+    const double *z0;
+    int64_t pz0;
+    double *roots;
+    int64_t proots;
+    int32_t *iters;   // nullptr: do not write statistics
+    int32_t *status;
+    double tol;
+    int32_t max_iter, win, kmin;
+    double radius;
+    long long watchdog;
+    int32_t max_degree;
+    const int32_t *order;  // nullptr: natural order
+    int *counter;          // persistent work queue
+};
+
+// block-wide max of two doubles and OR of a flag; result in sh
+__device__ void block_max2(DKShared &sh, double a, double b, int bad)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a = fmax(a, __shfl_down_sync(0xffffffffu, a, off));
+        b = fmax(b, __shfl_down_sync(0xffffffffu, b, off));
+        bad |= __shfl_down_sync(0xffffffffu, bad, off);
+    }
+    if (lane == 0) {
+        sh.red[0][warp] = a;
+        sh.red[1][warp] = b;
+        sh.redi[warp] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        int f = 0;
+        for (int w = 0; w < nw; w++) {
+            x = fmax(x, sh.red[0][w]);
+            y = fmax(y, sh.red[1][w]);
+            f |= sh.redi[w];
+        }
+        sh.delta = x;
+        sh.zmax = y;
+        sh.bad = f;
+    }
+    __syncthreads();
+}
+
+template <class P>
+__device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *smem)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t off = A.coef_off[b];
+    const int64_t n = A.coef_off[b + 1] - off - 1;
+    const int64_t ro = off - b;  // root offset
+    if (n <= 0 || n > A.max_degree) {
+        if (tid == 0 && A.iters) {
+            A.iters[b] = 0;
+            A.status[b] = n <= 0 ? DK_CONVERGED : DK_BREAKDOWN;
+        }
+        return;
+    }
+    const int64_t cap = (int64_t)A.max_degree + 1;  // coefficient plane stride
+    const int64_t zc = A.max_degree;                // iterate plane stride
+    double *c = smem;                               // K planes
+    double *z = c + K * cap;                        // 2K planes: current iterate
+    double *zn = A.roots + ro;                      // 2K planes, stride proots: next iterate
+    const int64_t pn = A.proots;
+
+    for (int64_t i = tid; i <= n; i += nt)
+        for (int cc = 0; cc < K; cc++) c[cc * cap + i] = A.coef[cc * A.pcoef + off + i];
+    __syncthreads();
+    // monic q_n = p_n / a_n unless a_n == 1 exactly
+    bool monic = c[n] == 1.0;
+    for (int cc = 1; cc < K; cc++) monic = monic && c[cc * cap + n] == 0.0;
+    if (!monic) {
+        const V inv = vrecip<P>(vload<P>(c, cap, n));
+        __syncthreads();
+        for (int64_t i = tid; i < n; i += nt) vstore<P>(c, cap, i, P::mul(vload<P>(c, cap, i), inv));
+        __syncthreads();
+        if (tid == 0)
+            for (int cc = 0; cc < K; cc++) c[cc * cap + n] = cc == 0 ? 1.0 : 0.0;
+        __syncthreads();
+    }
+
+    // starting values
+    if (A.z0) {
+        for (int64_t i = tid; i < n; i += nt)
+            for (int cc = 0; cc < 2 * K; cc++) z[cc * zc + i] = A.z0[cc * A.pz0 + ro + i];
+    } else {
+        double r = 0.0;
+        if (A.radius > 0.0) {
+            r = A.radius;
+        } else {
+            int cnt = 0;
+            for (int64_t i = tid; i < n; i += nt) cnt += c[i] != 0.0;
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if ((tid & 31) == 0) sh.redi[tid >> 5] = cnt;
+            __syncthreads();
+            if (tid == 0) {
+                int s = 0;
+                for (int w = 0; w < (nt + 31) / 32; w++) s += sh.redi[w];
+                sh.nnz = s;
+            }
+            __syncthreads();
+            const double nnz = (double)sh.nnz;
+            for (int64_t i = tid; i < n; i += nt) {
+                if (c[i] == 0.0) continue;
+                const double v = fabs(__dmul_rn(nnz, c[i]));
+                const double rt = dk_nthroot(v, n - i);
+                if (rt > r) r = rt;
+            }
+            block_max2(sh, r, 0.0, 0);
+            r = sh.delta;
+            if (r == 0.0) r = 1.0;
+        }
+        const double center = -__ddiv_rn(c[n - 1], (double)n);
+        for (int64_t i = tid; i < n; i += nt) {
+            const double th = __dadd_rn(__ddiv_rn(__dmul_rn(2.0 * (double)i, kPI), (double)n),
+                                        __ddiv_rn(3.0, 2.0 * (double)n));
+            double cs, sn;
+            dk_cos_sin(th, cs, sn);
+            for (int cc = 0; cc < 2 * K; cc++) z[cc * zc + i] = 0.0;
+            z[i] = __dadd_rn(center, __dmul_rn(r, cs));
+            z[K * zc + i] = __dmul_rn(r, sn);
+        }
+    }
+    __syncthreads();
+
+    const long long t0 = clock64();
+    int st = DK_CAP, it = A.max_iter;
+    double best = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    int since = 0;
+    for (int k = 1; k <= A.max_iter; k++) {
+        double dmax = 0.0, zm = 0.0;
+        int bad = 0;
+        for (int64_t i = tid; i < n; i += nt) {
+            const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
+            // q(z_i) with extended exponent
+            V hr = vload<P>(c, cap, n), hi = vzero<P>();
+            long long Eq = 0;
+            for (int64_t kk = n - 1; kk >= 0; kk--) {
+                V a = vload<P>(c, cap, kk);
+                if (Eq > 1000) a = vzero<P>();
+                else if (Eq > 0) vscale<P>(a, (int)-Eq);
+                V t1 = P::mul(hr, zr);
+                V t2 = P::mul(hi, zi);
+                t1 = vsub<P>(t1, t2);
+                t1 = P::add(t1, a);
+                V t3 = P::mul(hr, zi);
+                V t4 = P::mul(hi, zr);
+                hi = P::add(t3, t4);
+                hr = t1;
+                const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+                if (be >= 1023 + DK_RESCALE + 1) {
+                    vscale<P>(hr, -DK_RESCALE);
+                    vscale<P>(hi, -DK_RESCALE);
+                    Eq += DK_RESCALE;
+                }
+            }
+            // prod_{j != i} (z_i - z_j) with extended exponent
+            V dr = vone<P>(), di = vzero<P>();
+            long long Ed = 0;
+            for (int64_t j = 0; j < n; j++) {
+                if (j == i) continue;
+                const V tr = vsub<P>(zr, vload<P>(z, zc, j));
+                const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, j));
+                cmul<P>(dr, di, tr, ti, dr, di);
+                const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
+                if (be >= 1023 + DK_RESCALE + 1) {
+                    vscale<P>(dr, -DK_RESCALE);
+                    vscale<P>(di, -DK_RESCALE);
+                    Ed += DK_RESCALE;
+                } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
+                    vscale<P>(dr, DK_RESCALE);
+                    vscale<P>(di, DK_RESCALE);
+                    Ed -= DK_RESCALE;
+                }
+            }
+            V wr, wi;
+            cdiv<P>(hr, hi, dr, di, wr, wi);
+            vscale_big<P>(wr, Eq - Ed);
+            vscale_big<P>(wi, Eq - Ed);
+            const V yr = vsub<P>(zr, wr), yi = vsub<P>(zi, wi);
+            vstore<P>(zn, pn, i, yr);
+            vstore<P>(zn + K * pn, pn, i, yi);
+            const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
+            const double m = __dadd_rn(fabs(yr.c[0]), fabs(yi.c[0]));
+            if (!(d == d) || isinf(d) || !(m == m) || isinf(m)) bad = 1;
+            if (d > dmax) dmax = d;
+            if (m > zm) zm = m;
+        }
+        block_max2(sh, dmax, zm, bad);  // barrier: every read of the current iterate is done
+        for (int64_t i = tid; i < n; i += nt)  // each thread copies back the roots it wrote
+            for (int cc = 0; cc < 2 * K; cc++) z[cc * zc + i] = zn[cc * pn + i];
+        __syncthreads();
+        const double delta = sh.delta, zmax = sh.zmax;
+        const double scale = zmax > 1.0 ? zmax : 1.0;
+        if (sh.bad) { st = DK_BREAKDOWN; it = k; break; }
+        if (delta <= __dmul_rn(A.tol, scale)) { st = DK_CONVERGED; it = k; break; }
+        if (delta < best) { best = delta; since = 0; } else { since++; }
+        if (k >= A.kmin && since >= A.win && best <= __dmul_rn(pow2(-26 * K), scale)) {
+            st = DK_STAGNATED;
+            it = k;
+            break;
+        }
+        if (A.watchdog > 0) {
+            if (tid == 0) sh.stop = (clock64() - t0) > A.watchdog;
+            __syncthreads();
+            const int stop = sh.stop;
+            __syncthreads();
+            if (stop) { st = DK_TIMEOUT; it = k; break; }
+        }
+    }
+    for (int64_t i = tid; i < n; i += nt)  // (the start values when no sweep ran)
+        for (int cc = 0; cc < 2 * K; cc++) zn[cc * pn + i] = z[cc * zc + i];
+    if (tid == 0 && A.iters) {
+        A.iters[b] = it;
+        A.status[b] = st;
+    }
+    __syncthreads();
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_dk_persistent(DKArgs<P> A)
+{
+    extern __shared__ __align__(16) double dk_smem[];
+    __shared__ DKShared sh;
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int64_t p = next;
+        __syncthreads();
+        if (p >= A.npoly) break;
+        dk_solve<P>(A, A.order ? A.order[p] : p, sh, dk_smem);
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_dk_single(DKArgs<P> A, int64_t p)
+{
+    extern __shared__ __align__(16) double dk_smem[];
+    __shared__ DKShared sh;
+    dk_solve<P>(A, A.order ? A.order[p] : p, sh, dk_smem);
+}
+
+// Descending-degree order (ties by index): order[rank(p)] = p.
+__global__ void k_dk_order(int64_t npoly, const int64_t *__restrict__ coef_off, int32_t *__restrict__ order)
+{
+    __shared__ int64_t deg[1024];
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < npoly; p0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = p0 + threadIdx.x;
+        const int64_t dp = p < npoly ? coef_off[p + 1] - coef_off[p] : 0;
+        int64_t rank = 0;
+        for (int64_t q0 = 0; q0 < npoly; q0 += blockDim.x) {
+            __syncthreads();
+            if (q0 + threadIdx.x < npoly)
+                deg[threadIdx.x] = coef_off[q0 + threadIdx.x + 1] - coef_off[q0 + threadIdx.x];
+            __syncthreads();
+            const int64_t lim = npoly - q0 < blockDim.x ? npoly - q0 : blockDim.x;
+            for (int64_t j = 0; j < lim; j++) {
+                const int64_t dq = deg[j], q = q0 + j;
+                rank += (dq > dp) || (dq == dp && q < p);
+            }
+        }
+        if (p < npoly) order[rank] = (int32_t)p;
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(256) k_dk_start(int64_t npoly, const int64_t *coef_off, const double *coef,
+                                                  int64_t pcoef, double radius, int32_t max_degree, double *zout,
+                                                  int64_t pz)
+{
+    // Same start as dk_solve (monic normalisation included), without iterating.
+    extern __shared__ __align__(16) double dk_smem[];
+    __shared__ DKShared sh;
+    DKArgs<P> A{};
+    A.npoly = npoly;
+    A.coef_off = coef_off;
+    A.coef = coef;
+    A.pcoef = pcoef;
+    A.z0 = nullptr;
+    A.roots = zout;
+    A.proots = pz;
+    A.iters = nullptr;  // start values only: no per-polynomial statistics
+    A.status = nullptr;
+    A.max_iter = 0;
+    A.tol = 1.0;
+    A.win = 1;
+    A.kmin = 1;
+    A.radius = radius;
+    A.watchdog = 0;
+    A.max_degree = max_degree;
+    A.order = nullptr;
+    for (int64_t b = blockIdx.x; b < npoly; b += gridDim.x) dk_solve<P>(A, b, sh, dk_smem);
+}
+
+template <class P> static size_t dk_smem_bytes(int32_t max_degree)
+{
+    return (size_t)P::K * sizeof(double) * ((size_t)(max_degree + 1) + 2 * (size_t)max_degree);
+}
+
+constexpr size_t DK_SMEM_LIMIT = 227 * 1024 - 2048;  // leaves room for the static DKShared
+
+template <class P> static int32_t dk_max_degree()
+{
+    return (int32_t)((DK_SMEM_LIMIT / (P::K * sizeof(double)) - 1) / 3);
+}
+
+static size_t dk_ws(int64_t npoly) { return 256 + (size_t)(npoly > 0 ? npoly : 0) * sizeof(int32_t); }
+
+template <class P>
+static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,
+                              const double *z0, int64_t pz0, double *roots, int64_t proots, int32_t *iters,
+                              int32_t *status, const mp_roots_opts *o, void *ws, size_t ws_bytes, mp_stream s)
+{
+    if (npoly < 0 || o == nullptr) return MP_EINVAL;
+    if (npoly == 0) return MP_OK;
+    if (npoly > 0x7fffffff || coef_off == nullptr || coef == nullptr || roots == nullptr || iters == nullptr ||
+        status == nullptr || pcoef < 1 || proots < 1 || (z0 && pz0 < 1))
+        return MP_EINVAL;
+    if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
+    if (o->mode != 0 && o->mode != 1) return MP_EINVAL;
+    const int threads = o->threads > 0 ? o->threads : 128;
+    if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
+    if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
+    if (ws == nullptr) return MP_EINVAL;
+    if (ws_bytes < dk_ws(npoly)) return MP_ENOMEM;
+    cudaStream_t st = as_stream(s);
+    DKArgs<P> A{};
+    A.npoly = npoly;
+    A.coef_off = coef_off;
+    A.coef = coef;
+    A.pcoef = pcoef;
+    A.z0 = z0;
+    A.pz0 = pz0;
+    A.roots = roots;
+    A.proots = proots;
+    A.iters = iters;
+    A.status = status;
+    A.tol = o->tol > 0 ? o->tol : ldexp(1.0, -(53 * P::K - 6));
+    A.max_iter = o->max_iter > 0 ? o->max_iter : 1000;
+    A.win = o->stag_window > 0 ? o->stag_window : 5;
+    A.kmin = o->stag_min_iter > 0 ? o->stag_min_iter : 10;
+    A.radius = o->radius;
+    A.watchdog = o->watchdog_cycles;
+    A.max_degree = o->max_degree;
+    A.counter = static_cast<int *>(ws);
+    int32_t *order = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + 256);
+    A.order = nullptr;
+    const size_t smem = dk_smem_bytes<P>(o->max_degree);
+    if (o->sort) {
+        k_dk_order<<<grid_for(npoly, 256, 4), 256, 0, st>>>(npoly, coef_off, order);
+        mp_status e = launch_status();
+        if (e != MP_OK) return e;
+        A.order = order;
+    }
+    if (o->mode == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_dk_persistent<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        int per_sm = o->blocks_per_sm;
+        if (per_sm <= 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dk_persistent<P>, threads, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            if (per_sm < 1) per_sm = 1;
+        }
+        int64_t grid = (int64_t)sm_count() * per_sm;
+        if (grid > npoly) grid = npoly;
+        e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e);
+        k_dk_persistent<P><<<(unsigned)grid, threads, smem, st>>>(A);
+        return launch_status();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_dk_single<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int64_t p = 0; p < npoly; p++) {
+        k_dk_single<P><<<1, threads, smem, st>>>(A, p);
+        mp_status r = launch_status();
+        if (r != MP_OK) return r;
+    }
+    return MP_OK;
+}
+
+template <class P>
+static mp_status roots_init_launch(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,
+                                   double radius, int32_t max_degree, double *z, int64_t pz, mp_stream s)
+{
+    if (npoly < 0) return MP_EINVAL;
+    if (npoly == 0) return MP_OK;
+    if (coef_off == nullptr || coef == nullptr || z == nullptr || pcoef < 1 || pz < 1) return MP_EINVAL;
+    if (max_degree <= 0 || max_degree > dk_max_degree<P>()) return MP_EINVAL;
+    const size_t smem = dk_smem_bytes<P>(max_degree);
+    cudaError_t e = cudaFuncSetAttribute(k_dk_start<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    k_dk_start<P><<<grid_for(npoly, 1, 4), 256, smem, as_stream(s)>>>(npoly, coef_off, coef, pcoef, radius,
+                                                                      max_degree, z, pz);
+    return launch_status();
+}
+
+}  // namespace mp
+
+using namespace mp;
+
+extern "C" {
+
+#define MP_EXPORT_ROOTS(S, PT)                                                                        \
+    size_t mp_roots_workspace_##S(int64_t npoly) { return dk_ws(npoly); }                             \
+    int32_t mp_roots_max_degree_##S(void) { return dk_max_degree<PT>(); }                             \
+    mp_status mp_roots_init_##S(int64_t npoly, const int64_t *coef_off, const double *coef,            \
+                                int64_t pcoef, double radius, int32_t max_degree, double *z, int64_t pz, \
+                                mp_stream s)                                                          \
+    {                                                                                                 \
+        return roots_init_launch<PT>(npoly, coef_off, coef, pcoef, radius, max_degree, z, pz, s);     \
+    }                                                                                                 \
+    mp_status mp_roots_##S(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,  \
+                           const double *z0, int64_t pz0, double *roots, int64_t proots, int32_t *iters, \
+                           int32_t *status, const mp_roots_opts *opts, void *ws, size_t ws_bytes,      \
+                           mp_stream s)                                                               \
+    {                                                                                                 \
+        return roots_launch<PT>(npoly, coef_off, coef, pcoef, z0, pz0, roots, proots, iters, status,  \
+                                opts, ws, ws_bytes, s);                                               \
+    }
+
+MP_EXPORT_ROOTS(dd, P_dd)
+MP_EXPORT_ROOTS(ddc, P_ddc)
+MP_EXPORT_ROOTS(td, P_td)
+MP_EXPORT_ROOTS(qd, P_qd)
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+"""GPU parity: polynomial evaluation (Section 4.1), its adjoint, the
+polynomial builder, Aberth starting values (Eq. 5) and the Durand-Kerner solver
+(Eq. 4) through the C ABI against the CPU oracle -- all bit for bit (roots,
+iteration counts and statuses included)."""
+
+import numpy as np
+import pytest
+
+from paper_2603_14926_gb300 import inputs
+from test_gpu_blas import dev, host, same_bits
+
+pytestmark = pytest.mark.gpu
+
+
+def ragged(seed, npoly, dmin, dmax, K, dt):
+    rng = np.random.default_rng(seed)
+    deg = rng.integers(dmin, dmax + 1, npoly)
+    off = np.zeros(npoly + 1, dtype=np.int64)
+    np.cumsum(deg + 1, out=off[1:])
+    coef = inputs.mp_uniform(seed, int(off[-1]), K, dt, stream=inputs.STREAM_C)
+    return off, coef
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd", "ds", "tf", "qf"])
+def test_polyeval_bit_exact(mp, oracle, prec):
+    K, dt = oracle.PRECS[prec]
+    off, coef = ragged(1, 9, 0, 45, K, dt)
+    npts = 33
+    npoly = len(off) - 1
+    xr = inputs.mp_uniform(2, npoly * npts, K, dt, stream=inputs.STREAM_X)
+    xi = inputs.mp_uniform(3, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    doff, dcoef = dev(off), dev(coef)
+    y = mp.polyeval(prec, doff, dcoef, npts, dev(xr))
+    assert same_bits(host(y), oracle.polyeval(prec, off, coef, npts, xr))
+    yr, yi = mp.polyeval(prec, doff, dcoef, npts, dev(xr), dev(xi))
+    wr, wi = oracle.polyeval(prec, off, coef, npts, xr, xi)
+    assert same_bits(host(yr), wr) and same_bits(host(yi), wi)
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
+@pytest.mark.parametrize("npts", [1, 77])
+def test_polyeval_backward_bit_exact(mp, oracle, prec, npts):
+    """Degrees 0..70 span three 32-coefficient sweeps of the wavefront."""
+    K, dt = oracle.PRECS[prec]
+    off, coef = ragged(4, 7, 0, 70, K, dt)
+    off[2] = off[1]  # an empty polynomial (no coefficients)
+    npoly = len(off) - 1
+    x = inputs.mp_uniform(5, npoly * npts, K, dt, stream=inputs.STREAM_X)
+    dy = inputs.mp_uniform(6, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    dc, dx = mp.polyeval_backward(prec, dev(off), dev(coef), npts, dev(x), dev(dy))
+    wc, wx = oracle.polyeval_backward(prec, off, coef, npts, x, dy)
+    used = np.zeros(coef.shape[1], dtype=bool)
+    for b in range(npoly):
+        used[off[b]:off[b + 1]] = True
+    assert same_bits(host(dc)[:, used], wc[:, used])
+    assert same_bits(host(dx), wx)
+
+
+def test_polyeval_backward_workspace_checked(mp, oracle):
+    import torch
+
+    K, dt = 4, np.float64
+    off, coef = ragged(4, 3, 5, 9, K, dt)
+    x = dev(inputs.mp_uniform(5, 3 * 40, K, dt))
+    with pytest.raises(mp.MPError, match="workspace"):
+        mp.polyeval_backward("qd", dev(off), dev(coef), 40, x, x,
+                             ws=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    # dx alone needs no workspace
+    _, dx = mp.polyeval_backward("qd", dev(off), dev(coef), 40, x, x, want_dcoef=False)
+    assert dx.shape == (4, 120)
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
+def test_poly_from_roots_bit_exact(mp, oracle, prec):
+    prob = inputs.dk_problem(3, 11, 1, 75)
+    want = oracle.poly_from_roots(prec, prob)
+    got = mp.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta),
+                             int(prob.degrees.max()), int(prob.coef_off[-1]))
+    assert same_bits(host(got), want)
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+@pytest.mark.parametrize("radius", [0.0, 1.1])
+def test_roots_init_bit_exact(mp, oracle, prec, radius):
+    K = oracle.PRECS[prec][0]
+    prob = inputs.dk_problem(5, 7, 2, 90)
+    coef = oracle.poly_from_roots(prec, prob)
+    z = host(mp.roots_init(prec, dev(prob.coef_off), dev(coef), int(prob.degrees.max()), radius))
+    for b in range(prob.npoly):
+        c = coef[:, prob.coef_off[b]:prob.coef_off[b + 1]]
+        want = oracle.aberth(prec, c, radius)
+        assert same_bits(np.ascontiguousarray(z[:, prob.root_off[b]:prob.root_off[b + 1]]), want), b
+
+
+def _solve_both(mp, oracle, prec, prob, coef, **kw):
+    maxdeg = int(prob.degrees.max())
+    r, it, st = mp.roots(prec, dev(prob.coef_off), dev(coef), maxdeg, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("tol", "max_iter", "stag_window", "stag_min_iter",
+                                                  "radius")}
+    wr, wit, wst = oracle.roots(prec, prob.coef_off, coef, **okw)
+    return (host(r), host(it), host(st)), (wr, wit, wst)
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
+def test_roots_bit_exact(mp, oracle, prec):
+    prob = inputs.dk_problem(3, 6, 10, 40)
+    coef = oracle.poly_from_roots(prec, prob)
+    (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, prob, coef)
+    assert np.array_equal(it, wit) and np.array_equal(st, wst)
+    assert same_bits(np.ascontiguousarray(r), wr)
+    assert np.all((st == 1) | (st == 2))
+
+
+@pytest.mark.parametrize("mode,sort,threads", [(0, 0, 64), (0, 1, 256), (1, 0, 128), (1, 1, 32)])
+def test_roots_modes_identical(mp, oracle, mode, sort, threads):
+    """Persistent batched launch and the per-polynomial launch loop, sorted or not,
+    any block size: identical bits, equal to the oracle."""
+    prec = "td"
+    prob = inputs.dk_problem(8, 9, 3, 70)
+    coef = oracle.poly_from_roots(prec, prob)
+    (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, prob, coef, mode=mode, sort=sort,
+                                              threads=threads, radius=1.1)
+    assert np.array_equal(it, wit) and np.array_equal(st, wst)
+    assert same_bits(np.ascontiguousarray(r), wr)
+
+
+def test_roots_edge_cases(mp, oracle):
+    """Degree 0 and 1, a non-monic polynomial, an iteration cap, a non-finite
+    coefficient (breakdown), explicit starting values."""
+    prec, K = "qd", 4
+    prob = inputs.dk_problem(4, 3, 12, 20)
+    base = oracle.poly_from_roots(prec, prob)
+    three = np.zeros_like(base)
+    three[0] = 3.0
+    scaled = oracle.mul(prec, base, three)
+    lin = np.zeros((K, 3))
+    lin[0] = [5.0, 0.25, 1.0]  # degree 0 (a_0 = 5) and degree 1 (x + 0.25)
+    coef = np.concatenate([lin, scaled, base], 1)
+    off = np.concatenate([[0, 1, 3], 3 + prob.coef_off[1:], 3 + prob.coef_off[-1] + prob.coef_off[1:]])
+    bad = coef.copy()
+    bad[0, off[3] + 2] = np.nan
+
+    class Prob:
+        coef_off = off
+        degrees = np.diff(off) - 1
+    for c, kw in ((coef, {}), (coef, {"max_iter": 4}), (bad, {})):
+        (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, Prob, c, **kw)
+        assert np.array_equal(it, wit) and np.array_equal(st, wst), (kw, it, wit, st, wst)
+        ok = np.ones(r.shape[1], dtype=bool)
+        for b in np.nonzero(st == mp.DK_BREAKDOWN)[0]:  # NaN payloads are not compared
+            ok[off[b] - b:off[b + 1] - b - 1] = False
+        assert same_bits(np.ascontiguousarray(r[:, ok]), np.ascontiguousarray(wr[:, ok]))
+    assert np.sum(st == mp.DK_BREAKDOWN) == 1
+    z0 = mp.roots_init(prec, dev(off), dev(coef), int(Prob.degrees.max()))
+    r1, i1, s1 = mp.roots(prec, dev(off), dev(coef), int(Prob.degrees.max()))
+    r2, i2, s2 = mp.roots(prec, dev(off), dev(coef), int(Prob.degrees.max()), z0=z0)
+    assert same_bits(host(r1), host(r2)) and np.array_equal(host(i1), host(i2))
+
+
+def test_roots_watchdog_and_degree_bound(mp, oracle):
+    """A one-cycle watchdog ends every solve after its first sweep with status 3;
+    a polynomial above max_degree is skipped with status 4.  No fault, no hang."""
+    prec = "dd"
+    prob = inputs.dk_problem(6, 5, 20, 30)
+    coef = dev(oracle.poly_from_roots(prec, prob))
+    r, it, st = mp.roots(prec, dev(prob.coef_off), coef, int(prob.degrees.max()), watchdog_cycles=1)
+    assert np.all(host(st) == mp.DK_TIMEOUT) and np.all(host(it) == 1)
+    small = int(prob.degrees.min())
+    r, it, st = mp.roots(prec, dev(prob.coef_off), coef, small)
+    st = host(st)
+    assert np.all(st[prob.degrees > small] == mp.DK_BREAKDOWN)
+    assert np.all(st[prob.degrees == small] != mp.DK_BREAKDOWN)
+    with pytest.raises(mp.MPError, match="invalid"):
+        mp.roots(prec, dev(prob.coef_off), coef, mp.roots_max_degree(prec) + 1)
+
+
+def test_roots_batch_workload_sampled(mp, oracle):
+    """The batched-root workload's recipe (degrees uniform in [10, 500], roots in the
+    unit disk, 1e-30 perturbation, QD, start radius 1.1, persistent sorted launch) on
+    a 48-polynomial slice, 30 sweeps: GPU-built coefficients equal the oracle's on the
+    sampled polynomials; the per-polynomial launch loop reproduces the batched
+    launch bit for bit on the 8 lowest degrees; the 3 lowest equal the oracle's."""
+    prec = "qd"
+    prob = inputs.dk_problem(3, 48, 10, 500)
+    maxdeg = int(prob.degrees.max())
+    coef = mp.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), maxdeg,
+                              int(prob.coef_off[-1]))
+    hc = host(coef)
+    kw = dict(radius=1.1, max_iter=30)
+    r0, i0, s0 = mp.roots(prec, dev(prob.coef_off), coef, maxdeg, mode=0, sort=1, **kw)
+    r0, i0, s0 = host(r0), host(i0), host(s0)
+    small = np.argsort(prob.degrees, kind="stable")[:8]
+    sub_off = np.zeros(len(small) + 1, dtype=np.int64)
+    np.cumsum(prob.degrees[small] + 1, out=sub_off[1:])
+    sub_coef = np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in small], 1)
+    r1, i1, s1 = mp.roots(prec, dev(sub_off), dev(sub_coef), int(prob.degrees[small].max()),
+                          mode=1, **kw)
+    r1, i1, s1 = host(r1), host(i1), host(s1)
+    for q, b in enumerate(small):
+        lo, hi = prob.root_off[b], prob.root_off[b + 1]
+        assert same_bits(np.ascontiguousarray(r1[:, sub_off[q] - q:sub_off[q + 1] - q - 1]),
+                         np.ascontiguousarray(r0[:, lo:hi]))
+        assert i1[q] == i0[b] and s1[q] == s0[b]
+    for b in small[:3]:
+        sub = inputs.DKProblem([prob.degrees[b]], prob.rootdata[prob.root_off[b]:prob.root_off[b + 1]],
+                               prob.delta[prob.root_off[b]:prob.root_off[b + 1]])
+        c = oracle.poly_from_roots(prec, sub)
+        assert same_bits(np.ascontiguousarray(hc[:, prob.coef_off[b]:prob.coef_off[b + 1]]), c)
+        wr, wit, wst = oracle.roots(prec, sub.coef_off, c, **kw)
+        assert i0[b] == wit[0] and s0[b] == wst[0]
+        assert same_bits(np.ascontiguousarray(r0[:, prob.root_off[b]:prob.root_off[b + 1]]), wr)
