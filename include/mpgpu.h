@@ -175,6 +175,28 @@ const char *mp_version(void);
 /* dcoef != NULL, contents need no initialisation).                             */
 
 /* ------------------------------------------------------------------------ */
+/* mp_polyeval_backward_noalloc_qd: the QD Horner adjoint without a caller    */
+/* workspace, for code that cannot allocate device memory (a fixed memory     */
+/* pool that must not grow, a plugin whose allocator belongs to its host, a   */
+/* real-time loop where an allocation could stall).  The paper has no         */
+/* counterpart; this is a library convenience.  Same arguments and same       */
+/* results (bit for bit) as mp_polyeval_backward_qd without ws/ws_bytes.  Its  */
+/* scratch is a fixed 4 MiB device array inside the library, held by every GPU */
+/* that loads the library until the process exits, so dcoef requests need     */
+/* npoly * npts <= MP_NOALLOC_MAX_POINTS (131072 points); larger ones return  */
+/* MP_ENOMEM before anything is enqueued (dx-only calls have no limit).  The   */
+/* first call on a device looks the array up (cudaGetSymbolAddress) for that  */
+/* device, so make it before any stream capture.  Calls share the array:      */
+/* calls whose kernels overlap on the GPU race on it.  It needs no            */
+/* initialisation between calls.                                              */
+/* ------------------------------------------------------------------------ */
+#define MP_NOALLOC_MAX_POINTS (1 << 17)
+mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef,
+                                          int64_t pcoef, int64_t npts, const double *x, int64_t px,
+                                          const double *dy, int64_t pdy, double *dcoef, int64_t pdc,
+                                          double *dx, int64_t pdx, mp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* POLY_FROM_ROOTS: coefficients of prod (x - r) (the root-solving workload): */
 /* per polynomial, rootdata holds floor(n/2) complex roots as (re, im)      */
 /* pairs (conjugates implied) then one real root if n is odd; delta holds n */
