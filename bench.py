@@ -10,7 +10,7 @@ all ranks (each rank runs its own replica: weak scaling, no collective).
 
 Printed as ONE JSON line on rank 0, with the GEMM kernel's roofline against
 the FP64 pipe (the path is bound by FP64 instructions: 209 per QD multiply-add,
-see the design doc), the oracle's throughput on the host cores, an end-to-end figure
+Algorithms 13 and 14), the oracle's throughput on the host cores, an end-to-end figure
 with host-resident inputs, clocks sampled during the timed region, and (unless
 --no-extras) secondary measurements of the other kernels on bounded samples.
 
@@ -74,14 +74,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over all ranks (the slowest replica sets the job's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world, steps, work_per_step, max_time):
+    """Whole-job throughput: every rank runs `steps` replicas of the step."""
+    return world * steps * work_per_step / max_time
 
 
 # ---------------------------------------------------------------------------
@@ -250,6 +257,18 @@ def time_region(fn, steps, world, stream):
     return total, launches
 
 
+def gemm_traffic(prec, n):
+    """DRAM bytes per launch recorded by ncu for this kernel and size, if any."""
+    path = os.path.join(ROOT, "profiles", f"k_gemm_{prec}_{n}.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                return int(line.split(":", 1)[1].strip())
+    except OSError:
+        pass
+    return None
+
+
 def fp64_peak_live():
     import paper_2603_14926_gb300 as mpg
 
@@ -318,9 +337,20 @@ def extras(prec="qd", quick=False):
     return out
 
 
-def dk_extra(prec="qd", npoly=64, max_iter=30, loop_polys=8):
-    """Batched persistent DK (one launch, sorted queue) vs the per-polynomial launch
-    loop on the batched-root workload recipe (degrees in [10, 500])."""
+def dk_instr(prec, degrees, iters):
+    """FP64 instructions of the Durand-Kerner sweeps: per root and sweep, n complex
+    Horner steps (4 mul + 3 add) and n - 1 product steps (2 sub + 4 mul + 2 add)."""
+    d = degrees.astype(np.float64)
+    per_root = d * (4 * INSTR_MUL[prec] + 3 * INSTR_ADD[prec]) + (d - 1) * (4 * INSTR_MUL[prec] + 4 * INSTR_ADD[prec])
+    return float(np.sum(iters.astype(np.float64) * d * per_root))
+
+
+def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
+    """Batched persistent Durand-Kerner (one CUDA-graph replay: queue reset, degree
+    sort, persistent kernel) on the batched-root workload -- 4096 QD polynomials,
+    degrees uniform in [10, 500], roots in the unit disk, 1e-30 perturbation, start
+    radius 1.1 -- for a fixed number of sweeps, against the per-polynomial launch loop
+    on a degree-stratified sample of the same polynomials (same bits)."""
     import torch
 
     import paper_2603_14926_gb300 as mpg
@@ -332,36 +362,93 @@ def dk_extra(prec="qd", npoly=64, max_iter=30, loop_polys=8):
     coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), maxdeg,
                                int(prob.coef_off[-1]))
     off = dev(prob.coef_off)
-
-    def run(mode, o, c, md):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        r, it, st = mpg.roots(prec, o, c, md, radius=1.1, max_iter=max_iter, mode=mode, sort=1 - mode)
-        torch.cuda.synchronize()
-        return time.perf_counter() - t, it.cpu().numpy(), st.cpu().numpy()
-
-    run(0, off, coef, maxdeg)
-    tb, it, st = run(0, off, coef, maxdeg)
-    work = float(np.sum(prob.degrees.astype(np.float64) ** 2 * it))
-    pair = 8 * INSTR_MUL[prec] + 7 * INSTR_ADD[prec]
-    res = {"polys": npoly, "max_iter": max_iter, "batched_s": tb,
-           "batched_roots_per_s": float(prob.degrees.sum()) / tb,
-           "batched_root_iters_per_s": float(np.sum(prob.degrees * it)) / tb,
-           "batched_fp64_instr_frac": work * pair / tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
+    g = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=sweeps, sort=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r, it, st = g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    it, st, r = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
+    instr = dk_instr(prec, prob.degrees, it)
+    peak = NOMINAL_FP64_TFLOPS * 1e12 / 2
+    res = {"polys": npoly, "degrees": "uniform [10, 500]", "sweeps_cap": sweeps, "batched_graph_s": tb,
+           "root_sweeps_per_s": float(np.sum(prob.degrees * it)) / tb,
+           "fp64_instr_per_s": instr / tb, "fp64_instr_frac": instr / tb / peak,
            "status_counts": np.bincount(st, minlength=5).tolist()}
-    # per-polynomial launch loop on the lowest-degree `loop_polys` polynomials
-    sel = np.argsort(prob.degrees, kind="stable")[:loop_polys]
+    order = np.argsort(prob.degrees, kind="stable")
+    sel = order[np.linspace(0, npoly - 1, loop_polys).astype(int)]
     hc = coef.cpu().numpy()
     so = np.zeros(len(sel) + 1, dtype=np.int64)
     np.cumsum(prob.degrees[sel] + 1, out=so[1:])
     sc = np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in sel], 1)
+    dso, dsc = dev(so), dev(sc)
     md = int(prob.degrees[sel].max())
-    tl, itl, _ = run(1, dev(so), dev(sc), md)
-    tb2, itb, _ = run(0, dev(so), dev(sc), md)
-    res["loop_sample"] = {"polys": len(sel), "degrees": prob.degrees[sel].tolist(),
-                          "per_poly_loop_s": tl, "batched_s": tb2, "speedup": tl / tb2,
-                          "identical_iters": bool(np.array_equal(itl, itb))}
+    mpg.roots(prec, dso, dsc, md, radius=1.1, max_iter=1, mode=1)
+    torch.cuda.synchronize()
+    e0.record()
+    rl, itl, stl = mpg.roots(prec, dso, dsc, md, radius=1.1, max_iter=sweeps, mode=1)
+    e1.record()
+    torch.cuda.synchronize()
+    tl = e0.elapsed_time(e1) / 1e3
+    rl = rl.cpu().numpy()
+    same = all(np.array_equal(rl[:, so[q] - q:so[q + 1] - q - 1].view(np.uint64),
+                              np.ascontiguousarray(r[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
+               for q, b in enumerate(sel))
+    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy())
+    res["per_poly_loop_sample"] = {
+        "polys": len(sel), "degrees": prob.degrees[sel].tolist(), "loop_s": tl,
+        "fp64_instr_per_s": instr_l / tl, "identical_bits_to_batched": bool(same),
+        "batched_over_loop_throughput": (instr / tb) / (instr_l / tl),
+        "loop_s_extrapolated_to_all_polys": tl * instr / instr_l}
     return res
+
+
+def profile_one(a):
+    """One launch of a kernel family at the given size, for an ncu capture."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    mpg.load()
+    prec = a.prec
+    K = mpg.PRECS[prec][0]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    if a.profile == "gemm":
+        A, B = make_inputs(prec, a.n, a.seed)
+        mpg.gemm(prec, dev(A), dev(B))
+    elif a.profile in ("horner", "dcoef"):
+        npoly, deg, npts = a.n, 256, 4096
+        off = torch.arange(0, (npoly + 1) * (deg + 1), deg + 1, dtype=torch.int64, device="cuda")
+        coef = dev(inputs.mp_uniform(4, npoly * (deg + 1), K, stream=inputs.STREAM_C))
+        xs = dev(inputs.mp_uniform(5, npoly * npts, K, stream=inputs.STREAM_X))
+        if a.profile == "horner":
+            mpg.polyeval(prec, off, coef, npts, xs)
+        else:
+            mpg.polyeval_backward(prec, off, coef, npts, xs, xs, want_dx=False)
+    elif a.profile == "peak":
+        names = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "FFMA", 4: "FADD"}
+        res = {}
+        sms = mpg.lib().mp_sm_count()
+        for kind, nm in names.items():
+            it = 4096 if kind < 3 else 131072
+            best = 0.0
+            for per_sm, thr in ((2, 256), (4, 256), (8, 256), (8, 512)):
+                mpg.peak(kind, iters=256, blocks=sms * per_sm, threads=thr)
+                rate, _ = mpg.peak(kind, iters=it, blocks=sms * per_sm, threads=thr)
+                best = max(best, rate)
+            res[nm] = best / 1e9
+        print(json.dumps({"lane_instr_per_s_G": res, "sms": sms}))
+        return
+    elif a.profile == "dk":
+        prob = inputs.dk_problem(3, a.n, 10, 500)
+        md = int(prob.degrees.max())
+        coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), md,
+                                   int(prob.coef_off[-1]))
+        mpg.roots(prec, dev(prob.coef_off), coef, md, radius=1.1, max_iter=2, sort=1)
+    torch.cuda.synchronize()
+    print("ok", a.profile, a.n)
 
 
 def run_gpu(a, rank, world, pool):
@@ -385,7 +472,7 @@ def run_gpu(a, rank, world, pool):
         total, per_launch = time_region(step, a.steps, world, stream)
     total = max_over_ranks(total, world)
     ms_step = total / a.steps * 1e3
-    value = world * a.steps * 2.0 * n ** 3 / total
+    value = job_throughput(world, a.steps, 2.0 * n ** 3, total)
     launch_s = statistics.mean(per_launch)
     instr = n ** 3 * mac_instr(prec)
     peak_nominal = NOMINAL_FP64_TFLOPS * 1e12 / 2 / 1e9  # G FP64 instructions/s
@@ -397,8 +484,10 @@ def run_gpu(a, rank, world, pool):
                                "(152 SMs x 2 lanes/clk x 2.06 GHz)",
                 "peak_measured_live": peak_live, "frac_of_measured": achieved / peak_live,
                 "algorithmic_instr_per_launch": instr, "launch_ms": launch_s * 1e3,
-                "traffic": None,
-                "traffic_note": "DRAM bytes per launch: profiles/k_gemm_qd_2048.md (ncu)"}
+                "traffic": gemm_traffic(prec, n),
+                "traffic_source": "profiles/k_gemm_qd_2048.md (ncu dram__bytes_read.sum + "
+                                  "dram__bytes_write.sum, one launch of this kernel at this size)",
+                "algorithmic_bytes_per_launch": int(3 * A.nbytes)}
     # end to end through the public API with host-resident inputs
     hA = torch.from_numpy(A).pin_memory()
     hB = torch.from_numpy(B).pin_memory()
@@ -415,7 +504,7 @@ def run_gpu(a, rank, world, pool):
     torch.cuda.synchronize()
     te, _ = time_region(e2e_step, e2e_steps, world, stream)
     te = max_over_ranks(te, world)
-    e2e = {"value": world * e2e_steps * 2.0 * n ** 3 / te, "unit": "QD ops/s",
+    e2e = {"value": job_throughput(world, e2e_steps, 2.0 * n ** 3, te), "unit": "QD ops/s",
            "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(A.nbytes),
            "steps": e2e_steps}
     out = {"metric": "QD GEMM ops/s", "value": value, "unit": "QD ops/s", "n_gpus": world,
@@ -432,7 +521,7 @@ def run_gpu(a, rank, world, pool):
     if rank == 0 and not a.no_extras:
         try:
             ex = extras(prec, quick=a.quick)
-            ex["durand_kerner"] = dk_extra(prec)
+            ex["durand_kerner"] = dk_extra(prec, npoly=512 if a.quick else 4096)
             out["extra"] = ex
         except Exception as e:  # extras never hide the headline
             out["extra"] = {"error": repr(e)}
@@ -478,7 +567,12 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="smaller extras")
+    ap.add_argument("--profile", choices=["gemm", "horner", "dcoef", "dk", "peak"], default=None,
+                    help="run one launch of this kernel family at size --n (for ncu) and exit")
     a = ap.parse_args(argv)
+    if a.profile:
+        profile_one(a)
+        return 0
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))

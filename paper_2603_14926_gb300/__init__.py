@@ -273,8 +273,10 @@ def gemm_config_name(prec, c):
     return getattr(lib(), f"mp_gemm_config_name_{prec}")(c).decode()
 
 
-def gemm(prec, A, B, opA=0, opB=0, out=None, config=-1):
-    """C := op(A) op(B).  A is (K, m, k) for opA=0 or (K, k, m) for opA=1; likewise B."""
+def gemm(prec, A, B, opA=0, opB=0, out=None, config=None):
+    """C := op(A) op(B).  A is (K, m, k) for opA=0 or (K, k, m) for opA=1; likewise B.
+    config: a tile configuration index, -1 for the built-in choice, or None for the
+    autotuner's cached choice for this shape (built-in when none is cached)."""
     _check(prec, A, "A", 3)
     _check(prec, B, "B", 3)
     m, k = (A.shape[1], A.shape[2]) if not opA else (A.shape[2], A.shape[1])
@@ -285,6 +287,10 @@ def gemm(prec, A, B, opA=0, opB=0, out=None, config=-1):
         if X[0].stride(1) != 1:
             raise ValueError(f"{nm} rows must be contiguous")
     out = empty(prec, m, n, device=A.device) if out is None else _check(prec, out, "out", 3)
+    if config is None:
+        from .tune import best_gemm_config
+
+        config = best_gemm_config(prec, m, n, k)
     _call(f"mp_gemm_ex_{prec}", int(opA), int(opB), m, n, k, _ptr(A), A[0].stride(0), _ps(A),
           _ptr(B), B[0].stride(0), _ps(B), _ptr(out), out[0].stride(0), _ps(out), int(config),
           _stream())
@@ -384,6 +390,51 @@ def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_w
           z0.stride(0) if z0 is not None else 0, _ptr(r), r.stride(0), _ptr(iters),
           _ptr(status), ctypes.byref(o), _ptr(ws), ws.numel(), _stream())
     return r[:, :total], iters, status
+
+
+class RootsGraph:
+    """The persistent batched Durand-Kerner solve (work-queue reset, optional
+    descending-degree order, one persistent launch) captured once in a CUDA graph
+    and replayed.  Outputs live in preallocated tensors: .roots, .iters, .status.
+    Options as for roots(); mode must be 0."""
+
+    def __init__(self, prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0,
+                 stag_window=0, stag_min_iter=0, radius=0.0, watchdog_cycles=0, threads=0,
+                 blocks_per_sm=0, sort=1):
+        t = _torch()
+        _check(prec, coef, "coef", 2)
+        K = PRECS[prec][0]
+        self.prec, self.coef_off, self.coef, self.z0 = prec, coef_off, coef, z0
+        self.npoly = coef_off.numel() - 1
+        self.total = coef.shape[1] - self.npoly
+        dev = coef.device
+        self._r = t.zeros((2 * K, max(self.total, 1)), dtype=coef.dtype, device=dev)
+        self.iters = t.zeros(self.npoly, dtype=t.int32, device=dev)
+        self.status = t.zeros(self.npoly, dtype=t.int32, device=dev)
+        self.ws = t.empty(max(roots_workspace(prec, self.npoly), 1), dtype=t.uint8, device=dev)
+        self.opts = RootsOpts(tol, max_iter, stag_window, stag_min_iter, 0, radius, watchdog_cycles,
+                              int(max_degree), threads, blocks_per_sm, sort)
+        self._launch()  # first launch outside capture: function attributes, module load
+        t.cuda.synchronize()
+        self.graph = t.cuda.CUDAGraph()
+        with t.cuda.graph(self.graph):
+            self._launch()
+        t.cuda.synchronize()
+
+    def _launch(self):
+        z0 = self.z0
+        _call(f"mp_roots_{self.prec}", self.npoly, _ptr(self.coef_off), _ptr(self.coef),
+              _ps(self.coef), _ptr(z0), z0.stride(0) if z0 is not None else 0, _ptr(self._r),
+              self._r.stride(0), _ptr(self.iters), _ptr(self.status), ctypes.byref(self.opts),
+              _ptr(self.ws), self.ws.numel(), _stream())
+
+    @property
+    def roots(self):
+        return self._r[:, :self.total]
+
+    def replay(self):
+        self.graph.replay()
+        return self.roots, self.iters, self.status
 
 
 def peak(kind, iters=4096, blocks=None, threads=256):

@@ -7,7 +7,10 @@
 // Design.  Every output c_ij is the sequential fold over l = 0..k-1 of
 // c = add(c, mul(a_il, b_lj)) from c = 0, the operation order of the naive
 // triple loop, so results are bit-identical to the CPU oracle; k is never split.
-// A block owns a BM x BN tile of C; each thread owns a TM x TN register
+// A block owns a BM x BN tile of C, in grouped order: consecutive blocks walk
+// down GEMM_GROUP tile rows before moving one tile column right, so the blocks
+// resident at any moment cover a near-square patch of C and the op(A) and op(B)
+// slabs they read fit in L2 together.  Each thread owns a TM x TN register
 // micro-tile (TM*TN independent multiply-add chains for instruction-level
 // parallelism).  K-component tiles of op(A) and op(B), BK deep, are staged in
 // shared memory component-plane by component-plane, loaded so that consecutive
@@ -35,6 +38,8 @@ struct GemmCfg {
     static_assert(NT % 32 == 0 && NT <= 1024, "threads");
 };
 
+constexpr int64_t GEMM_GROUP = 16;  // tile rows per group of the block order
+
 template <class P, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
     k_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const typename P::T *__restrict__ A,
@@ -50,7 +55,13 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
 
     const int tid = threadIdx.x;
     const int tx = tid % G::NTX, ty = tid / G::NTX;
-    const int64_t i0 = (int64_t)blockIdx.y * BM, j0 = (int64_t)blockIdx.x * BN;
+    // grouped block order (1-D grid of tm * tn blocks)
+    const int64_t tm = (m + BM - 1) / BM, tn = (n + BN - 1) / BN;
+    const int64_t per_group = GEMM_GROUP * tn;
+    const int64_t L = blockIdx.x, g = L / per_group, first = g * GEMM_GROUP;
+    const int64_t rows = tm - first < GEMM_GROUP ? tm - first : GEMM_GROUP;
+    const int64_t r_in = L - g * per_group;
+    const int64_t i0 = (first + r_in % rows) * BM, j0 = (r_in / rows) * BN;
 
     V acc[TM][TN];
 #pragma unroll
@@ -117,8 +128,8 @@ static mp_status gemm_run(int opA, int opB, int64_t m, int64_t n, int64_t k, con
 {
     using G = GemmCfg<P, BM, BN, BK, TM, TN>;
     const int64_t gx = (n + BN - 1) / BN, gy = (m + BM - 1) / BM;
-    if (gx > 0x7fffffff || gy > 65535) return MP_EINVAL;
-    dim3 grid((unsigned)gx, (unsigned)gy);
+    if (gx * gy > 0x7fffffff) return MP_EINVAL;
+    dim3 grid((unsigned)(gx * gy));
     k_gemm<P, BM, BN, BK, TM, TN><<<grid, G::NT, 0, s>>>(opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C,
                                                           ldc, pC);
     return launch_status();
