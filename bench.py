@@ -428,7 +428,8 @@ def profile_one(a):
         else:
             mpg.polyeval_backward(prec, off, coef, npts, xs, xs, want_dx=False)
     elif a.profile == "peak":
-        names = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "FFMA", 4: "FADD"}
+        names = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "FFMA", 4: "FADD", 5: "FFMA2 (f32x2, per lane)",
+                 6: "FADD2 (f32x2, per lane)"}
         res = {}
         sms = mpg.lib().mp_sm_count()
         for kind, nm in names.items():

@@ -297,9 +297,10 @@ MPGPU_DECL_ROOTS(qd)
 /* Pipe-peak microbenchmark (measurement support, not part of the method):   */
 /* `blocks` x `threads` threads each run `iters` iterations of 8 independent */
 /* dependency chains of one instruction kind: 0 = DFMA, 1 = DADD, 2 = DMUL,  */
-/* 3 = FFMA, 4 = FADD.  SYNCHRONIZES the stream; *ms receives the elapsed    */
-/* time between CUDA events recorded on it and *lane_ops the number of      */
-/* per-lane instructions executed (blocks * threads * iters * 8).           */
+/* 3 = FFMA, 4 = FADD, 5 = packed fma.rn.f32x2, 6 = packed add.rn.f32x2.     */
+/* SYNCHRONIZES the stream; *ms receives the elapsed time between CUDA      */
+/* events recorded on it and *lane_ops the number of per-lane operations     */
+/* executed (blocks * threads * iters * 8, doubled for the packed kinds).   */
 /* ------------------------------------------------------------------------ */
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms,
                       double *lane_ops, mp_stream stream);

@@ -231,10 +231,39 @@ static mp_status gemv_launch(int64_t m, int64_t n, const typename P::T *A, int64
 // Pipe-peak microbenchmark: 8 independent chains per thread.
 // ---------------------------------------------------------------------------
 
+// Packed binary32 pairs (sm_100+ PTX): two lanes per instruction.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c)
+{
+    unsigned long long d;
+    asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm volatile("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 template <int KIND>
 __global__ void k_peak(int64_t iters, double *sink)
 {
-    if (KIND <= 2) {
+    if (KIND >= 5) {
+        unsigned long long a[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = 0x3f8000003f800000ULL + threadIdx.x + j;  // ~(1.0f, 1.0f)
+        const unsigned long long b = 0x3f7fffff3f7fffffULL, cc = 0x2edbe6ff2edbe6ffULL;
+        for (int64_t it = 0; it < iters; it++) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) a[j] = KIND == 5 ? ffma2(a[j], b, cc) : fadd2(a[j], cc);
+        }
+        unsigned long long s = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) s ^= a[j];
+        if (s == 12345ULL) sink[0] = (double)s;
+    } else if (KIND <= 2) {
         double a[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) a[j] = 1.0 + 1e-9 * (threadIdx.x + 8 * j);
@@ -298,7 +327,7 @@ int mp_sm_count(void) { return sm_count(); }
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms, double *lane_ops,
                       mp_stream stream)
 {
-    if (kind < 0 || kind > 4 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
+    if (kind < 0 || kind > 6 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
         ms == nullptr || lane_ops == nullptr)
         return MP_EINVAL;
     cudaStream_t s = as_stream(stream);
@@ -316,13 +345,15 @@ mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *m
     case 1: k_peak<1><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 2: k_peak<2><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 3: k_peak<3><<<blocks, threads, 0, s>>>(iters, nullptr); break;
-    default: k_peak<4><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 4: k_peak<4><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 5: k_peak<5><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    default: k_peak<6><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     }
     st = launch_status();
     cudaEventRecord(e1, s);
     if (st == MP_OK) st = cuda_status(cudaEventSynchronize(e1));
     if (st == MP_OK) st = cuda_status(cudaEventElapsedTime(ms, e0, e1));
-    *lane_ops = (double)blocks * threads * (double)iters * 8.0;
+    *lane_ops = (double)blocks * threads * (double)iters * 8.0 * (kind >= 5 ? 2.0 : 1.0);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
