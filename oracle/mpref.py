@@ -12,9 +12,12 @@ have 2K planes: real components then imaginary components.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
+import shutil
 import subprocess
+import tempfile
 import threading
 
 import numpy as np
@@ -70,6 +73,41 @@ def lib(counting: bool = False) -> ctypes.CDLL:
             _declare(L)
             _libs[counting] = L
         return _libs[counting]
+
+
+@contextlib.contextmanager
+def mutant(replacements):
+    """Temporarily route every call to a build of the oracle with source edits
+    applied: `replacements` is a list of (file, old, new) string substitutions,
+    each of which must match exactly once.  Used by the tests that plant
+    mistakes in the oracle to show that its pins catch them."""
+    with tempfile.TemporaryDirectory() as d:
+        for f in ("mpref.c", "mpref_core.inc", "mpref_dk.inc"):
+            shutil.copy(os.path.join(HERE, f), d)
+        for f, old, new in replacements:
+            path = os.path.join(d, f)
+            src = open(path).read()
+            if src.count(old) != 1:
+                raise ValueError(f"mutation does not match exactly once in {f}: {old!r}")
+            open(path, "w").write(src.replace(old, new))
+        libs = {}
+        for counting in (False, True):
+            out = os.path.join(d, f"m{int(counting)}.so")
+            subprocess.run(["gcc", *_CFLAGS, *(["-DMPREF_COUNT"] if counting else []),
+                            os.path.join(d, "mpref.c"), "-lm", "-o", out], check=True)
+            L = ctypes.CDLL(out)
+            _declare(L)
+            libs[counting] = L
+        with _lock:
+            saved = dict(_libs)
+            _libs.clear()
+            _libs.update(libs)
+        try:
+            yield
+        finally:
+            with _lock:
+                _libs.clear()
+                _libs.update(saved)
 
 
 _i64 = ctypes.c_int64
