@@ -319,6 +319,19 @@ def extras(prec="qd", quick=False):
     t = timed(lambda: mpg.gemv(prec, A, xv, out=yv))
     out["gemv"] = {"m": m, "n": m, "ms": t * 1e3, "fp64_instr_frac": m * m * ins / t / peak}
     del A
+    # complex GEMM by the 3M method (Eq. 3) vs the real GEMM, n = 1024, Eq. 2 entries
+    nc = 512 if quick else 1024
+    Ur, Er, Ui, Ei = inputs.complex_eq2(7, (nc, nc), K)
+    mk = lambda U, E: mpg.mul(prec, dev(U.reshape(K, -1)),  # noqa: E731
+                              dev(inputs.mp_from_double(E.reshape(-1), K))).reshape(K, nc, nc)
+    Ar, Ai, Br, Bi = mk(Ur, Er), mk(Ui, Ei), mk(Ur, Ei), mk(Ui, Er)
+    Cr, Ci = mpg.empty(prec, nc, nc), mpg.empty(prec, nc, nc)
+    tc = timed(lambda: mpg.cgemm(prec, Ar, Ai, Br, Bi, out=(Cr, Ci)), reps=1)
+    tr = timed(lambda: mpg.gemm(prec, Ar, Br, out=Cr), reps=1)
+    out["complex_gemm_3m"] = {"n": nc, "ms": tc * 1e3, "real_gemm_ms": tr * 1e3, "complex_over_real": tc / tr,
+                              "complex_qd_ops_per_s": 8.0 * nc ** 3 / tc,
+                              "fp64_instr_frac": 3 * nc ** 3 * ins / tc / peak}
+    del Ar, Ai, Br, Bi, Cr, Ci
     # Horner forward/backward: 1024 polynomials, degree 256, 4096 real points each
     npoly, deg, npts = (256 if quick else 1024), 256, 4096
     off = torch.arange(0, (npoly + 1) * (deg + 1), deg + 1, dtype=torch.int64, device="cuda")
@@ -402,6 +415,62 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
         "batched_over_loop_throughput": (instr / tb) / (instr_l / tl),
         "loop_s_extrapolated_to_all_polys": tl * instr / instr_l}
     return res
+
+
+def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None):
+    """The paper's Durand-Kerner problem (Section 4.2, Eq. 6, n = 64; Table 6): one solve
+    on the GPU (latency), a batch of `copies` identical problems in one persistent
+    launch (throughput), and the oracle's single solve on one host core."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    K = mpg.PRECS[prec][0]
+    c = inputs.rational_to_mp(inputs.chebyshev_quadrature(n), K)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    off1 = dev(np.array([0, n + 1], dtype=np.int64))
+    c1 = dev(c)
+    mpg.roots(prec, off1, c1, n)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r, it, st = mpg.roots(prec, off1, c1, n)
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1) / 1e3
+    offb = dev(np.arange(0, (n + 1) * (copies + 1), n + 1, dtype=np.int64))
+    cb = dev(np.tile(c, copies))
+    g = mpg.RootsGraph(prec, offb, cb, n)
+    e0.record()
+    rb, itb, stb = g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    res = {"n": n, "precision": prec, "sweeps": int(it.cpu()[0]), "status": int(st.cpu()[0]),
+           "single_solve_gpu_s": t1, "batch_copies": copies, "batch_s": tb,
+           "batch_solves_per_s": copies / tb,
+           "batch_fp64_instr_frac": dk_instr(prec, np.full(copies, n), itb.cpu().numpy()) / tb /
+           (NOMINAL_FP64_TFLOPS * 1e12 / 2),
+           "paper_table6_s": {"EPYC BF AVX2": 0.415, "EPYC BF": 0.628, "Snapdragon BF Neon": 0.336,
+                              "Snapdragon BF": 0.383}}
+    if pool is not None:
+        res["oracle_single_core_s"] = pool.pool.apply(_oracle_chebyshev, ((prec, n),))
+    return res
+
+
+def _oracle_chebyshev(args):
+    prec, n = args
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from oracle import mpref
+    from paper_2603_14926_gb300 import inputs
+
+    K = mpref.PRECS[prec][0]
+    c = inputs.rational_to_mp(inputs.chebyshev_quadrature(n), K)
+    t = time.perf_counter()
+    mpref.roots(prec, np.array([0, n + 1]), c)
+    return time.perf_counter() - t
 
 
 def profile_one(a):
@@ -523,6 +592,7 @@ def run_gpu(a, rank, world, pool):
         try:
             ex = extras(prec, quick=a.quick)
             ex["durand_kerner"] = dk_extra(prec, npoly=512 if a.quick else 4096)
+            ex["chebyshev_dk"] = chebyshev_extra(prec, copies=512 if a.quick else 4096, pool=pool)
             out["extra"] = ex
         except Exception as e:  # extras never hide the headline
             out["extra"] = {"error": repr(e)}

@@ -142,6 +142,25 @@ const char *mp_version(void);
     const char *mp_gemm_config_name_##P(int config);
 
 /* ------------------------------------------------------------------------ */
+/* CGEMM  complex C := op(A) op(B) by the 3M method (Section 3.2, Eq. 3):     */
+/*   C1 = Re A Re B, C2 = Im A Im B, Re C = C1 - C2,                          */
+/*   Im C = (Re A + Im A)(Re B + Im B) - C1 - C2 (subtracted left to right), */
+/* three mp_gemm_ex_P products plus elementwise sums and differences; the    */
+/* operand sums are formed in the operands' own storage layout.  Real and    */
+/* imaginary parts are separate K-arrays sharing lda/pA (A), ldb/pB (B),     */
+/* ldc/pC (C); layouts and op as for GEMM.  Bit-identical to the CPU oracle. */
+/* ws: DEVICE workspace of mp_cgemm_workspace_P(m, n, pA, pB) bytes (the two */
+/* operand sums and C2; no initialisation needed).  Cr, Ci must not alias   */
+/* the inputs.                                                              */
+/* ------------------------------------------------------------------------ */
+#define MPGPU_DECL_CGEMM(P, T)                                                              \
+    size_t mp_cgemm_workspace_##P(int64_t m, int64_t n, int64_t pA, int64_t pB);            \
+    mp_status mp_cgemm_##P(int opA, int opB, int64_t m, int64_t n, int64_t k, const T *Ar,  \
+                           const T *Ai, int64_t lda, int64_t pA, const T *Br, const T *Bi,  \
+                           int64_t ldb, int64_t pB, T *Cr, T *Ci, int64_t ldc, int64_t pC,  \
+                           void *ws, size_t ws_bytes, mp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* POLYEVAL  (Section 4.1) batched Horner evaluation of real-coefficient    */
 /* polynomials p_b(x) = sum_{i=0}^{n_b} a_{b,i} x^i.                        */
 /*   coef_off : DEVICE int64[npoly+1]; polynomial b owns coefficients        */
@@ -279,6 +298,7 @@ typedef struct {
     MPGPU_DECL_DOT(P, T)                                                                    \
     MPGPU_DECL_GEMV(P, T)                                                                   \
     MPGPU_DECL_GEMM(P, T)                                                                   \
+    MPGPU_DECL_CGEMM(P, T)                                                                  \
     MPGPU_DECL_POLY(P, T)
 
 MPGPU_DECL_ALL(dd, double)

@@ -127,6 +127,8 @@ def _declare(L):
             "gemv": [_i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp, _i64],
             "gemm": [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64,
                      _i64, _vp, _i64, _i64],
+            "cgemm": [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp,
+                      _i64, _i64, _vp, _vp, _i64, _i64],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                   _vp, _i64],
@@ -275,6 +277,21 @@ def gemm(prec, A, B, opA=0, opB=0, rows=None):
         getattr(lib(), f"mpref_gemm_{prec}")(opA, opB, r1 - r0, n, k, _vp(Ap), lda, A[0].size,
                                              _p(B), ldb, B[0].size, _p(C), n, C[0].size)
     return C
+
+
+def cgemm(prec, Ar, Ai, Br, Bi, opA=0, opB=0):
+    """Complex C := op(A) op(B) by the 3M method (Eq. 3); returns (Re C, Im C)."""
+    Ar, Ai, Br, Bi = (_arr(x, prec) for x in (Ar, Ai, Br, Bi))
+    K = Ar.shape[0]
+    m, k = (Ar.shape[1], Ar.shape[2]) if not opA else (Ar.shape[2], Ar.shape[1])
+    k2, n = (Br.shape[1], Br.shape[2]) if not opB else (Br.shape[2], Br.shape[1])
+    assert k == k2
+    Cr = np.zeros((K, m, n), dtype=Ar.dtype)
+    Ci = np.zeros_like(Cr)
+    getattr(lib(), f"mpref_cgemm_{prec}")(opA, opB, m, n, k, _p(Ar), _p(Ai), Ar.shape[2],
+                                          Ar[0].size, _p(Br), _p(Bi), Br.shape[2], Br[0].size,
+                                          _p(Cr), _p(Ci), n, max(m * n, 1))
+    return Cr, Ci
 
 
 # ---------------------------------------------------------------------------

@@ -70,6 +70,8 @@ def _declare(L):
                      _i64, _vp],
             "gemm_ex": [_int, _int, _i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp,
                         _i64, _i64, _int, _vp],
+            "cgemm": [_int, _int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _i64,
+                      _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                   _vp, _i64, _vp, ctypes.c_size_t, _vp],
@@ -84,6 +86,8 @@ def _declare(L):
         getattr(L, f"mp_dot_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_polyeval_backward_workspace_{p}").argtypes = [_i64, _i64]
         getattr(L, f"mp_polyeval_backward_workspace_{p}").restype = ctypes.c_size_t
+        getattr(L, f"mp_cgemm_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
+        getattr(L, f"mp_cgemm_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
         getattr(L, f"mp_gemm_config_name_{p}").argtypes = [_int]
         getattr(L, f"mp_gemm_config_name_{p}").restype = ctypes.c_char_p
@@ -295,6 +299,28 @@ def gemm(prec, A, B, opA=0, opB=0, out=None, config=None):
           _ptr(B), B[0].stride(0), _ps(B), _ptr(out), out[0].stride(0), _ps(out), int(config),
           _stream())
     return out
+
+
+def cgemm(prec, Ar, Ai, Br, Bi, opA=0, opB=0, out=None, ws=None):
+    """Complex C := op(A) op(B) by the 3M method; returns (Re C, Im C)."""
+    t = _torch()
+    for X, nm in ((Ar, "Ar"), (Ai, "Ai"), (Br, "Br"), (Bi, "Bi")):
+        _check(prec, X, nm, 3)
+    if Ai.shape != Ar.shape or Bi.shape != Br.shape or Ai.stride() != Ar.stride() or Bi.stride() != Br.stride():
+        raise ValueError("real and imaginary parts must share shape and strides")
+    m, k = (Ar.shape[1], Ar.shape[2]) if not opA else (Ar.shape[2], Ar.shape[1])
+    k2, n = (Br.shape[1], Br.shape[2]) if not opB else (Br.shape[2], Br.shape[1])
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} vs {k2}")
+    Cr, Ci = out if out is not None else (empty(prec, m, n, device=Ar.device),
+                                          empty(prec, m, n, device=Ar.device))
+    nb = int(getattr(lib(), f"mp_cgemm_workspace_{prec}")(m, n, _ps(Ar), _ps(Br)))
+    if ws is None:
+        ws = t.empty(max(nb, 1), dtype=t.uint8, device=Ar.device)
+    _call(f"mp_cgemm_{prec}", int(opA), int(opB), m, n, k, _ptr(Ar), _ptr(Ai), Ar[0].stride(0), _ps(Ar),
+          _ptr(Br), _ptr(Bi), Br[0].stride(0), _ps(Br), _ptr(Cr), _ptr(Ci), Cr[0].stride(0), _ps(Cr),
+          _ptr(ws), ws.numel(), _stream())
+    return Cr, Ci
 
 
 # ---------------------------------------------------------------------------

@@ -196,6 +196,61 @@ def dk_problem_from_roots(root_lists, perturb: float = 0.0) -> DKProblem:
                      np.full(total, perturb, dtype=np.float64))
 
 
+def complex_eq2(seed: int, shape, K: int, dtype=np.float64) -> tuple:
+    """Factors of the complex GEMM test matrices (Section 3.2, Eq. 2):
+    a = exp(r_n) (r_u - 1/2) + exp(r_n) (r_u - 1/2) sqrt(-1), every draw
+    independent.  Returns (Ur, Er, Ui, Ei) for the real and imaginary parts:
+    U = r_u - 1/2 as a full-precision K-component number (the nonoverlapping
+    generator, halved: exact) and E = exp(r_n) in binary64 (r_n standard normal
+    by Box-Muller).  The entry is the K-component product U * E, which callers
+    form with their multiply (the one place multicomponent arithmetic enters)."""
+    shape = tuple(np.atleast_1d(shape).tolist())
+    count = int(np.prod(shape))
+    base = (int(seed) * 0x100000001B3 + STREAM_C + 7) & 0xFFFFFFFFFFFFFFFF
+    out = []
+    for part in range(2):
+        U = mp_uniform(seed, shape, K, dtype, stream=STREAM_C + 11 + part) * dtype(0.5)
+        u1 = uniform01(base, count, (2 * part) * count)
+        u2 = uniform01(base, count, (2 * part + 1) * count)
+        rn = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+        out += [U, np.exp(rn).reshape(shape)]
+    return tuple(out)
+
+
+def chebyshev_quadrature(n: int):
+    """Exact rational coefficients a_0..a_n of the Chebyshev integration problem
+    (Section 4.2, Eq. 6), the monic polynomial whose roots are the n Chebyshev
+    quadrature nodes: power sums sum x^k = n/(k+1) for even k and 0 for odd k,
+    turned into coefficients by Newton's identities:
+        a_n = 1,  a_{n-(2k-1)} = 0,
+        a_{n-2k} = -(n / (2k)) * sum_{j=1..k} a_{n-2(k-j)} / (2j+1),  k = 1..n/2.
+    (The printed Eq. 6 is garbled; this reading keeps its surviving terms and
+    gives x^2 - 1/3 for n = 2 and x^3 - x/2 for n = 3.)"""
+    from fractions import Fraction
+
+    a = [Fraction(0)] * (n + 1)
+    a[n] = Fraction(1)
+    for k in range(1, n // 2 + 1):
+        s = sum(a[n - 2 * (k - j)] / (2 * j + 1) for j in range(1, k + 1))
+        a[n - 2 * k] = -Fraction(n, 2 * k) * s
+    return a
+
+
+def rational_to_mp(values, K: int, dtype=np.float64) -> np.ndarray:
+    """K-array of the greedy K-component expansions of exact rationals
+    (component j = the rounding of what components 0..j-1 leave)."""
+    from fractions import Fraction
+
+    out = np.zeros((K, len(values)), dtype=dtype)
+    for i, v in enumerate(values):
+        r = Fraction(v)
+        for j in range(K):
+            c = dtype(float(r))
+            out[j, i] = c
+            r -= Fraction(float(c))
+    return out
+
+
 def horner_points(seed: int, npoly: int, npts: int) -> np.ndarray:
     """Real evaluation points uniform in [-1, 1): shape (npoly, npts), binary64."""
     base = (int(seed) * 0x100000001B3 + STREAM_X) & 0xFFFFFFFFFFFFFFFF

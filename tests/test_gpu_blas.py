@@ -174,3 +174,40 @@ def test_gemm_full_size_sampled(mp, oracle, prec, n):
 def test_peak_microbenchmark_runs(mp):
     rate, ms = mp.peak(0, iters=256)
     assert rate > 0 and ms > 0
+
+
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd", "qf"])
+@pytest.mark.parametrize("opA,opB", [(0, 0), (1, 1)])
+def test_cgemm3m_bit_exact(mp, oracle, prec, opA, opB):
+    """3M complex GEMM (Eq. 3): both parts bit for bit, ragged sizes, op modes."""
+    K, dt = oracle.PRECS[prec]
+    m, n, k = 37, 45, 29
+    sa = (k, m) if opA else (m, k)
+    sb = (n, k) if opB else (k, n)
+    Ar, Ai = inputs.mp_uniform(1, sa, K, dt), inputs.mp_uniform(2, sa, K, dt)
+    Br, Bi = inputs.mp_uniform(3, sb, K, dt), inputs.mp_uniform(4, sb, K, dt)
+    wr, wi = oracle.cgemm(prec, Ar, Ai, Br, Bi, opA, opB)
+    gr, gi = mp.cgemm(prec, dev(Ar), dev(Ai), dev(Br), dev(Bi), opA, opB)
+    assert same_bits(host(gr), wr) and same_bits(host(gi), wi)
+
+
+def test_cgemm3m_eq2_matrices(mp, oracle):
+    """Eq. 2 matrices, QD, n = 96 (entries U * exp(r_n) formed on the GPU with mp_mul,
+    which the oracle's multiply reproduces bit for bit)."""
+    prec, K, n = "qd", 4, 96
+
+    def mats(seed):
+        Ur, Er, Ui, Ei = inputs.complex_eq2(seed, (n, n), K)
+        out = []
+        for U, E in ((Ur, Er), (Ui, Ei)):
+            g = mp.mul(prec, dev(U.reshape(K, -1)), dev(inputs.mp_from_double(E.reshape(-1), K)))
+            w = oracle.mul(prec, U.reshape(K, -1), inputs.mp_from_double(E.reshape(-1), K))
+            assert same_bits(host(g), w)
+            out.append(w.reshape(K, n, n))
+        return out
+
+    Ar, Ai = mats(1)
+    Br, Bi = mats(2)
+    wr, wi = oracle.cgemm(prec, Ar, Ai, Br, Bi)
+    gr, gi = mp.cgemm(prec, dev(Ar), dev(Ai), dev(Br), dev(Bi))
+    assert same_bits(host(gr), wr) and same_bits(host(gi), wi)

@@ -209,3 +209,22 @@ def test_roots_batch_workload_sampled(mp, oracle):
         wr, wit, wst = oracle.roots(prec, sub.coef_off, c, **kw)
         assert i0[b] == wit[0] and s0[b] == wst[0]
         assert same_bits(np.ascontiguousarray(r0[:, prob.root_off[b]:prob.root_off[b + 1]]), wr)
+
+
+@pytest.mark.parametrize("prec,n", [("qd", 64), ("td", 64), ("dd", 32)])
+def test_roots_chebyshev_bit_exact(mp, oracle, prec, n):
+    """The paper's Durand-Kerner test problem (Section 4.2, Eq. 6; Table 6 uses n = 64),
+    started from Eq. 5 as printed: roots, sweeps and status equal the oracle's, both as a
+    single solve and as one member of a batch of identical problems."""
+    K = oracle.PRECS[prec][0]
+    c = inputs.rational_to_mp(inputs.chebyshev_quadrature(n), K)
+    wr, wit, wst = oracle.roots(prec, np.array([0, n + 1]), c)
+    r, it, st = mp.roots(prec, dev(np.array([0, n + 1])), dev(c), n)
+    assert host(it)[0] == wit[0] and host(st)[0] == wst[0]
+    assert same_bits(host(r), wr)
+    copies = 5
+    cb = np.tile(c, copies)
+    ob = np.arange(0, (n + 1) * (copies + 1), n + 1, dtype=np.int64)
+    rb, itb, stb = mp.roots(prec, dev(ob), dev(cb), n)
+    assert np.all(host(itb) == wit[0]) and np.all(host(stb) == wst[0])
+    assert same_bits(host(rb), np.tile(wr, copies))

@@ -183,3 +183,65 @@ def test_reductions_edge_cases(oracle, prec):
     E = np.zeros((K, 3, 0), dtype=dt)
     F = np.zeros((K, 0, 5), dtype=dt)
     assert np.array_equal(oracle.gemm(prec, E, F), np.zeros((K, 3, 5)))
+
+
+def eq2_matrices(oracle, prec, seed, n):
+    """Eq. 2 entries U * exp(r_n), the product formed with the oracle's multiply."""
+    K, dt = oracle.PRECS[prec]
+    Ur, Er, Ui, Ei = inputs.complex_eq2(seed, (n, n), K, dt)
+    mk = lambda U, E: oracle.mul(prec, U.reshape(K, -1),  # noqa: E731
+                                 inputs.mp_from_double(E.reshape(-1), K, dt)).reshape(K, n, n)
+    return mk(Ur, Er), mk(Ui, Ei)
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_cgemm3m_vs_exact_and_paper_digits(oracle, prec):
+    """3M complex GEMM (Eq. 3) on Eq. 2 matrices.  Every entry within the bound of
+    its three real products and two subtractions; the worst entry keeps at least
+    the lower end of the digits the paper reports (Section 3.2: DD 23.2, TD 39.2,
+    QD 55.8 -- measured there with Strassen up to n = 2049) and no more than the
+    format holds."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_accuracy.json")))
+    lo, hi = g["complex_gemm_digits"][prec]
+    K = oracle.PRECS[prec][0]
+    p = pbits(oracle, prec)
+    n = 32
+    Ar, Ai = eq2_matrices(oracle, prec, 1, n)
+    Br, Bi = eq2_matrices(oracle, prec, 2, n)
+    Cr, Ci = oracle.cgemm(prec, Ar, Ai, Br, Bi)
+    iar, iai, ibr, ibi = (mp_ints(x) for x in (Ar, Ai, Br, Bi))
+    er = iar.dot(ibr) - iai.dot(ibi)
+    ei = iar.dot(ibi) + iai.dot(ibr)
+    f = lambda X: np.abs(X.astype(np.float64)).sum(0)  # noqa: E731
+    sa, sb = f(Ar) + f(Ai), f(Br) + f(Bi)
+    mag = sa @ sb  # bounds |Re A||Re B| + |Im A||Im B| + |Re A + Im A||Re B + Im B| sums
+    digits = math.inf
+    for got, ex in ((mp_ints(Cr), er), (mp_ints(Ci), ei)):
+        for i in range(n):
+            for j in range(n):
+                e = abs(got[i, j] * (1 << SCALE_BITS) - ex[i, j])
+                assert float(Fraction(e, 1 << (2 * SCALE_BITS))) <= 3 * reduction_bound(n, p) * mag[i, j]
+                if e:
+                    digits = min(digits, -math.log10(float(Fraction(e, abs(ex[i, j])))))
+    assert lo <= digits <= K * 53 * math.log10(2) + 1.5, digits
+
+
+def test_cgemm3m_structure(oracle):
+    """Re C = C1 - C2 and Im C = (C3 - C1) - C2 with C1, C2, C3 the oracle's real GEMMs,
+    in transposed storage too; a real input (Im = 0) reduces to the real GEMM."""
+    prec, K = "qd", 4
+    m, n, k = 5, 7, 6
+    Ar, Ai = inputs.mp_uniform(1, (m, k), K), inputs.mp_uniform(2, (m, k), K)
+    Br, Bi = inputs.mp_uniform(3, (k, n), K), inputs.mp_uniform(4, (k, n), K)
+    Cr, Ci = oracle.cgemm(prec, Ar, Ai, Br, Bi)
+    C1 = oracle.gemm(prec, Ar, Br)
+    C2 = oracle.gemm(prec, Ai, Bi)
+    C3 = oracle.gemm(prec, oracle.add(prec, Ar, Ai), oracle.add(prec, Br, Bi))
+    assert np.array_equal(Cr, oracle.add(prec, C1, -C2))
+    assert np.array_equal(Ci, oracle.add(prec, oracle.add(prec, C3, -C1), -C2))
+    tr = lambda X: np.ascontiguousarray(X.transpose(0, 2, 1))  # noqa: E731
+    Tr, Ti = oracle.cgemm(prec, tr(Ar), tr(Ai), tr(Br), tr(Bi), opA=1, opB=1)
+    assert np.array_equal(Tr, Cr) and np.array_equal(Ti, Ci)
+    Z = np.zeros_like(Ai)
+    Rr, Ri = oracle.cgemm(prec, Ar, Z, Br, np.zeros_like(Bi))
+    assert np.array_equal(Rr, oracle.gemm(prec, Ar, Br)) and not np.any(Ri)

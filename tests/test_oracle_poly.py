@@ -423,3 +423,45 @@ def test_dk_high_degree_extended_exponent(oracle):
         # the start Eq. 5 gives without the explicit radius is far larger
         z0 = oracle.aberth(prec, coef)
         assert np.max(np.abs(z0[0] + 1j * z0[K])) > 2.0
+
+
+def test_chebyshev_coefficients_closed_forms():
+    """The reading of Eq. 6 (Newton's identities on the power sums n/(k+1)) gives the
+    classical Chebyshev quadrature polynomials for n = 2..5."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "chebyshev_quadrature.json")))
+    for n, coefs in g["coefficients_low_to_high"].items():
+        assert inputs.chebyshev_quadrature(int(n)) == [Fraction(c) for c in coefs], n
+    # power sums of the n = 64 polynomial's roots are n/(k+1) (even k) and 0 (odd k):
+    # checked through the Newton identities in reverse for the first ten
+    a = inputs.chebyshev_quadrature(64)
+    n = 64
+    e = [Fraction(1)] + [(-1) ** k * a[n - k] for k in range(1, 11)]  # elementary symmetric
+    p = [None]
+    for k in range(1, 11):
+        pk = (-1) ** (k - 1) * k * e[k] + sum((-1) ** (k - 1 + i) * e[k - i] * p[i] for i in range(1, k))
+        p.append(pk)
+        assert pk == (Fraction(n, k + 1) if k % 2 == 0 else 0), k
+
+
+@pytest.mark.parametrize("prec", ["td", "qd"])
+def test_dk_chebyshev_n4_nodes(oracle, prec):
+    """x^4 - 2/3 x^2 + 1/45 has the nodes +-sqrt(1/3 +- 2/(3 sqrt5)) (the paper's problem
+    at n = 4, started from Eq. 5 as printed)."""
+    K = oracle.PRECS[prec][0]
+    p = pbits(oracle, prec)
+    c = inputs.rational_to_mp(inputs.chebyshev_quadrature(4), K)
+    r, it, st = oracle.roots(prec, np.array([0, 5]), c)
+    assert st[0] in (oracle.DK_CONVERGED, oracle.DK_STAGNATED)
+    s5 = isqrt_frac(Fraction(5), 400)
+    nodes = []
+    for sgn in (1, -1):
+        x2 = Fraction(1, 3) + sgn * Fraction(2, 3) / s5
+        x = isqrt_frac(x2, 300)
+        nodes += [x, -x]
+    got = sorted(mp_value(r[:K, j]) for j in range(4))
+    for g_, w in zip(got, sorted(nodes)):
+        assert float(abs(g_ - w)) <= 2.0 ** -(p - 10)
+    assert all(float(abs(mp_value(r[K:, j]))) <= 2.0 ** -(p - 10) for j in range(4))
