@@ -548,7 +548,8 @@ def run_gpu(a, rank, world, pool):
     peak_nominal = NOMINAL_FP64_TFLOPS * 1e12 / 2 / 1e9  # G FP64 instructions/s
     achieved = instr / launch_s / 1e9
     peak_live = fp64_peak_live() / 1e9
-    roofline = {"bound": "alu", "kernel": f"k_gemm<P_{prec}> (FP64 pipe)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": f"k_gemm_tma<P_{prec}, 32, 32, 16, 2, 2> (TMA-staged tiles; FP64 pipe)",
+                "achieved": achieved,
                 "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
                 "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2) -> 625 G FP64 instructions/s "
                                "(152 SMs x 2 lanes/clk x 2.06 GHz)",

@@ -130,6 +130,12 @@ const char *mp_version(void);
 /* the result is bit-identical to the CPU oracle.  C must not alias A or B. */
 /* mp_gemm_ex_P selects a tile configuration (0 .. mp_gemm_num_configs_P()-1,*/
 /* or -1 for the built-in choice); configurations differ only in speed.     */
+/* Configuration 4 stages the tiles with TMA (cp.async.bulk.tensor, double  */
+/* buffered on mbarriers) when the operands meet TMA's alignment rules      */
+/* (16-byte aligned base, lda/ldb and plane strides multiples of 16 bytes)  */
+/* and otherwise runs configuration 0.  mp_gemm_tma_timeouts_P SYNCHRONIZES */
+/* and reports how many TMA waits ever ran out (always 0 unless the copy    */
+/* path failed; the kernel then returns early instead of hanging).          */
 /* ------------------------------------------------------------------------ */
 #define MPGPU_DECL_GEMM(P, T)                                                               \
     mp_status mp_gemm_##P(int opA, int opB, int64_t m, int64_t n, int64_t k, const T *A,    \
@@ -139,6 +145,7 @@ const char *mp_version(void);
                              int64_t lda, int64_t pA, const T *B, int64_t ldb, int64_t pB,  \
                              T *C, int64_t ldc, int64_t pC, int config, mp_stream stream);  \
     int mp_gemm_num_configs_##P(void);                                                      \
+    mp_status mp_gemm_tma_timeouts_##P(unsigned int *count);                                \
     const char *mp_gemm_config_name_##P(int config);
 
 /* ------------------------------------------------------------------------ */

@@ -89,6 +89,8 @@ def _declare(L):
         getattr(L, f"mp_cgemm_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
         getattr(L, f"mp_cgemm_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
+        getattr(L, f"mp_gemm_tma_timeouts_{p}").argtypes = [ctypes.POINTER(ctypes.c_uint)]
+        getattr(L, f"mp_gemm_tma_timeouts_{p}").restype = _int
         getattr(L, f"mp_gemm_config_name_{p}").argtypes = [_int]
         getattr(L, f"mp_gemm_config_name_{p}").restype = ctypes.c_char_p
     for p in DK_PRECS:
@@ -170,7 +172,9 @@ def _check(prec, x, name, ndim=None):
         raise ValueError(f"{name}: expected {K} component planes, got shape {tuple(x.shape)}")
     if ndim is not None and x.dim() != ndim:
         raise ValueError(f"{name}: expected {ndim} dims, got {tuple(x.shape)}")
-    if not x[0].is_contiguous():
+    if x.dim() >= 2 and x.shape[-1] > 1 and x.stride(-1) != 1:
+        raise ValueError(f"{name}: the last dimension must be contiguous (unit stride)")
+    if x.dim() == 2 and not x[0].is_contiguous():
         raise ValueError(f"{name}: each component plane must be contiguous")
     return x
 
@@ -271,6 +275,13 @@ def gemv(prec, A, x, out=None):
 
 def gemm_num_configs(prec):
     return int(getattr(lib(), f"mp_gemm_num_configs_{prec}")())
+
+
+def gemm_tma_timeouts(prec):
+    """How many TMA waits of the TMA-staged GEMM ran out (synchronizes; 0 normally)."""
+    v = ctypes.c_uint()
+    _call(f"mp_gemm_tma_timeouts_{prec}", ctypes.byref(v))
+    return v.value
 
 
 def gemm_config_name(prec, c):

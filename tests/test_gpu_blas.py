@@ -211,3 +211,30 @@ def test_cgemm3m_eq2_matrices(mp, oracle):
     wr, wi = oracle.cgemm(prec, Ar, Ai, Br, Bi)
     gr, gi = mp.cgemm(prec, dev(Ar), dev(Ai), dev(Br), dev(Bi))
     assert same_bits(host(gr), wr) and same_bits(host(gi), wi)
+
+
+@pytest.mark.parametrize("prec", ["qd", "dd", "qf"])
+def test_gemm_tma_config_layouts(mp, oracle, prec):
+    """The TMA-staged configuration (4): TMA-eligible layouts (even leading dimensions)
+    and ineligible ones (odd lda/ldb: the plain kernel runs instead) both give the
+    oracle's bits, in every operand mode, and no TMA wait ever runs out."""
+    import torch
+
+    K, dt = oracle.PRECS[prec]
+    m, n, k = 67, 53, 90
+    for pad in (0, 1, 2):  # storage padded to a leading dimension of cols + pad
+        for opA, opB in ((0, 0), (1, 0), (0, 1), (1, 1)):
+            sa = (k, m) if opA else (m, k)
+            sb = (n, k) if opB else (k, n)
+            A = inputs.mp_uniform(11, sa, K, dt)
+            B = inputs.mp_uniform(12, sb, K, dt)
+            Ap = np.zeros((K, sa[0], sa[1] + pad), dtype=dt)
+            Ap[:, :, :sa[1]] = A
+            Bp = np.zeros((K, sb[0], sb[1] + pad), dtype=dt)
+            Bp[:, :, :sb[1]] = B
+            dA = dev(Ap)[:, :, :sa[1]]
+            dB = dev(Bp)[:, :, :sb[1]]
+            got = host(mp.gemm(prec, dA, dB, opA, opB, config=4))
+            assert same_bits(got, oracle.gemm(prec, A, B, opA, opB)), (pad, opA, opB)
+    torch.cuda.synchronize()
+    assert mp.gemm_tma_timeouts(prec) == 0
