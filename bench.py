@@ -473,6 +473,72 @@ def _oracle_chebyshev(args):
     return time.perf_counter() - t
 
 
+def roots_workload(a):
+    """The batched-root workload solved to the end: 4096 QD polynomials, degrees
+    uniform in [10, 500], roots in the unit disk, 1e-30 perturbation, start radius
+    1.1, at most --max-iter sweeps; one CUDA-graph replay (queue reset, descending
+    degree order, persistent kernel).  Then the per-polynomial launch loop on a
+    degree-stratified sample, to the end as well, with identical bits."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    mpg.load()
+    prec = a.prec
+    prob = inputs.dk_problem(3, a.npoly, 10, 500)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    maxdeg = int(prob.degrees.max())
+    coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), maxdeg,
+                               int(prob.coef_off[-1]))
+    off = dev(prob.coef_off)
+    # constructing the graph runs the solve once outside capture: that run is the warm-up
+    g = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=a.max_iter, sort=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record()
+        r, it, st = g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    it, st, r = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
+    instr = dk_instr(prec, prob.degrees, it)
+    order = np.argsort(prob.degrees, kind="stable")
+    sel = order[np.linspace(0, a.npoly - 1, a.loop_polys).astype(int)]
+    hc = coef.cpu().numpy()
+    so = np.zeros(len(sel) + 1, dtype=np.int64)
+    np.cumsum(prob.degrees[sel] + 1, out=so[1:])
+    sc = np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in sel], 1)
+    md = int(prob.degrees[sel].max())
+    e0.record()
+    rl, itl, stl = mpg.roots(prec, dev(so), dev(sc), md, radius=1.1, max_iter=a.max_iter, mode=1)
+    e1.record()
+    torch.cuda.synchronize()
+    tl = e0.elapsed_time(e1) / 1e3
+    rl = rl.cpu().numpy()
+    same = all(np.array_equal(rl[:, so[q] - q:so[q + 1] - q - 1].view(np.uint64),
+                              np.ascontiguousarray(r[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
+               for q, b in enumerate(sel))
+    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy())
+    roots_total = int(prob.degrees.sum())
+    out = {"metric": "batched roots/s", "value": roots_total / tb, "unit": "roots/s",
+           "higher_is_better": True, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{a.npoly} {prec.upper()} polynomials, degrees uniform [10, 500], roots "
+                                  "in the unit disk, 1e-30 perturbation, start radius 1.1, "
+                                  f"<= {a.max_iter} sweeps; one CUDA-graph replay"},
+           "batched_s": tb, "roots": roots_total, "sweeps_mean": float(it.mean()), "sweeps_max": int(it.max()),
+           "status_counts": {"cap": int(np.sum(st == 0)), "converged": int(np.sum(st == 1)),
+                             "stagnated": int(np.sum(st == 2)), "breakdown": int(np.sum(st == 4))},
+           "fp64_instr_per_s": instr / tb, "fp64_instr_frac": instr / tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
+           "per_poly_loop_sample": {"polys": len(sel), "degrees": prob.degrees[sel].tolist(),
+                                    "sweeps": itl.cpu().numpy().tolist(), "loop_s": tl,
+                                    "identical_bits_to_batched": bool(same),
+                                    "roots_per_s": float(prob.degrees[sel].sum()) / tl,
+                                    "batched_over_loop_throughput": (instr / tb) / (instr_l / tl)},
+           "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def profile_one(a):
     """One launch of a kernel family at the given size, for an ncu capture."""
     import torch
@@ -639,11 +705,20 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="smaller extras")
+    ap.add_argument("--workload", choices=["gemm", "roots"], default="gemm",
+                    help="gemm: the QD GEMM benchmark line (default); roots: the batched-root "
+                         "workload solved to the end (a separate, longer measurement)")
+    ap.add_argument("--npoly", type=int, default=4096)
+    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--loop-polys", type=int, default=8)
     ap.add_argument("--profile", choices=["gemm", "horner", "dcoef", "dk", "peak"], default=None,
                     help="run one launch of this kernel family at size --n (for ncu) and exit")
     a = ap.parse_args(argv)
     if a.profile:
         profile_one(a)
+        return 0
+    if a.workload == "roots" and a.impl == "gb300":
+        roots_workload(a)
         return 0
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")

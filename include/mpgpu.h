@@ -99,7 +99,8 @@ const char *mp_version(void);
 /* Each thread folds a strided subsequence with add(acc, mul(x_i, y_i)),    */
 /* partial sums are combined by warp shuffles and a block tree using the    */
 /* multicomponent add itself, then one block combines the block partials in */
-/* a fixed order: deterministic, but not the oracle's sequential order --   */
+/* a fixed order (one full wave of SMs x resident blocks): deterministic on */
+/* a given GPU model, but not the oracle's sequential order --              */
 /* it agrees with the exact sum within (4n+16) 2^-p sum |x_i y_i|, p = K*53 */
 /* (binary64) or K*24 (binary32).  ws: device workspace of at least         */
 /* mp_dot_workspace_P(n) bytes (MP_ENOMEM if smaller); it holds the block   */
@@ -112,9 +113,11 @@ const char *mp_version(void);
 
 /* ------------------------------------------------------------------------ */
 /* GEMV  y := A x, A m x n row-major (leading dimension lda >= n, plane     */
-/* stride pA).  One warp per row: lane l folds columns l, l+32, ... then a  */
-/* shuffle tree with the multicomponent add; deterministic, within the dot  */
-/* bound above of the exact result.  y must not alias A or x.               */
+/* stride pA).  Each row is folded by T threads (T in 32..256, chosen from  */
+/* m, n and the SM count): thread t folds columns t, t+T, ..., a warp       */
+/* shuffle tree and then the row's warps in order combine the partials     */
+/* with the multicomponent add; deterministic on a given GPU model, within */
+/* the dot bound above of the exact result.  y must not alias A or x.      */
 /* ------------------------------------------------------------------------ */
 #define MPGPU_DECL_GEMV(P, T)                                                               \
     mp_status mp_gemv_##P(int64_t m, int64_t n, const T *A, int64_t lda, int64_t pA,        \

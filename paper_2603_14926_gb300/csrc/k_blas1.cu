@@ -140,13 +140,30 @@ template <class P> __device__ __forceinline__ typename P::V block_reduce(typenam
 }
 
 constexpr int DOT_THREADS = 256;
-constexpr int64_t DOT_MAX_BLOCKS = 1024;
 
-// Fixed block count (independent of the device) so results are reproducible everywhere.
-static int64_t dot_blocks(int64_t n)
+template <class P>
+__global__ void __launch_bounds__(DOT_THREADS) k_dot_partial(int64_t n, const typename P::T *__restrict__ x,
+                                                             int64_t px, const typename P::T *__restrict__ y,
+                                                             int64_t py, typename P::T *__restrict__ part);
+
+// One full wave of resident blocks (SMs x blocks per SM), so every block folds the
+// same number of elements and no partial last wave idles the FP64 pipe.  The count
+// depends only on the device, so results are reproducible on a given GPU model.
+template <class P> static int64_t dot_blocks(int64_t n)
 {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dot_partial<P>, DOT_THREADS, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        cached[dev] = sm_count() * per_sm;
+    }
     int64_t g = (n + DOT_THREADS - 1) / DOT_THREADS;
-    if (g > DOT_MAX_BLOCKS) g = DOT_MAX_BLOCKS;
+    if (g > cached[dev]) g = cached[dev];
     return g < 1 ? 1 : g;
 }
 
@@ -175,7 +192,7 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dot_final(int64_t g, const type
 
 template <class P> static size_t dot_ws(int64_t n)
 {
-    return (size_t)dot_blocks(n < 0 ? 0 : n) * P::K * sizeof(typename P::T);
+    return (size_t)dot_blocks<P>(n < 0 ? 0 : n) * P::K * sizeof(typename P::T);
 }
 
 template <class P>
@@ -185,7 +202,7 @@ static mp_status dot_launch(int64_t n, const typename P::T *x, int64_t px, const
     if (n < 0 || result == nullptr || !planes_ok(x, n, px) || !planes_ok(y, n, py) || ws == nullptr)
         return MP_EINVAL;
     if (ws_bytes < dot_ws<P>(n)) return MP_ENOMEM;
-    int64_t g = dot_blocks(n);
+    int64_t g = dot_blocks<P>(n);
     auto *part = static_cast<typename P::T *>(ws);
     k_dot_partial<P><<<(unsigned)g, DOT_THREADS, 0, as_stream(s)>>>(n, x, px, y, py, part);
     mp_status st = launch_status();
@@ -195,22 +212,51 @@ static mp_status dot_launch(int64_t n, const typename P::T *x, int64_t px, const
 }
 
 // ---------------------------------------------------------------------------
-// GEMV: one warp per row
+// GEMV: one warp per row for short rows, one 256-thread block per row for long
+// ones (many more, smaller work units than resident warps, so no tail wave)
 // ---------------------------------------------------------------------------
 
 template <class P>
 __global__ void __launch_bounds__(256) k_gemv(int64_t m, int64_t n, const typename P::T *__restrict__ A,
                                               int64_t lda, int64_t pA, const typename P::T *__restrict__ x,
-                                              int64_t px, typename P::T *__restrict__ y, int64_t py)
+                                              int64_t px, typename P::T *__restrict__ y, int64_t py, int per_row)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= m) return;  // whole warp leaves together
+    // per_row threads fold one row; blockDim / per_row rows per block
+    const int t = threadIdx.x % per_row;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / per_row) + threadIdx.x / per_row;
     typename P::V acc = vzero<P>();
-    const typename P::T *Ar = A + row * lda;
-    for (int64_t j = lane; j < n; j += 32) acc = P::add(acc, P::mul(vload<P>(Ar, pA, j), vload<P>(x, px, j)));
+    if (row < m) {
+        const typename P::T *Ar = A + row * lda;
+        for (int64_t j = t; j < n; j += per_row)
+            acc = P::add(acc, P::mul(vload<P>(Ar, pA, j), vload<P>(x, px, j)));
+    }
     acc = warp_reduce<P>(acc);
-    if (lane == 0) vstore<P>(y, py, row, acc);
+    if (per_row > 32) {  // combine the row's warps (per_row / 32 of them) in shared memory
+        __shared__ typename P::T red[P::K][8];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < P::K; c++) red[c][warp] = acc.c[c];
+        __syncthreads();
+        if (t == 0) {
+            const int w0 = warp;  // first warp of this row
+            typename P::V s = vload<P>(&red[0][0], 8, w0);
+            for (int w = 1; w < per_row / 32; w++) s = P::add(s, vload<P>(&red[0][0], 8, w0 + w));
+            acc = s;
+        }
+    }
+    if (t == 0 && row < m) vstore<P>(y, py, row, acc);
+}
+
+// Threads per row: the smallest of 32, 64, 128, 256 that gives at least 8 full
+// waves of warps (so the last, partial wave costs little), as long as each thread
+// still folds at least 16 columns (so the reduction tree stays cheap).
+static int gemv_threads_per_row(int64_t m, int64_t n)
+{
+    const int64_t resident_warps = (int64_t)sm_count() * 24;  // 3 blocks of 8 warps per SM
+    int t = 32;
+    while (t < 256 && m * (t / 32) < 8 * resident_warps && n / (2 * t) >= 16) t *= 2;
+    return t;
 }
 
 template <class P>
@@ -221,9 +267,10 @@ static mp_status gemv_launch(int64_t m, int64_t n, const typename P::T *A, int64
     if (m < 0 || n < 0 || lda < n || !planes_ok(y, m, py) || !planes_ok(x, n, px)) return MP_EINVAL;
     if (m > 0 && n > 0 && (A == nullptr || pA < (m - 1) * lda + n)) return MP_EINVAL;
     if (m == 0) return MP_OK;
-    int64_t blocks = (m + 7) / 8;
+    const int per_row = gemv_threads_per_row(m, n);
+    const int64_t blocks = (m + (256 / per_row) - 1) / (256 / per_row);
     if (blocks > 0x7fffffff) return MP_EINVAL;
-    k_gemv<P><<<(unsigned)blocks, 256, 0, as_stream(s)>>>(m, n, A, lda, pA, x, px, y, py);
+    k_gemv<P><<<(unsigned)blocks, 256, 0, as_stream(s)>>>(m, n, A, lda, pA, x, px, y, py, per_row);
     return launch_status();
 }
 

@@ -99,9 +99,11 @@ def test_dot_workspace_errors(mp):
 
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "tf"])
-def test_gemv_within_bound(mp, oracle, prec):
+@pytest.mark.parametrize("n", [1029, 2500])
+def test_gemv_within_bound(mp, oracle, prec, n):
+    """n < 2048: a warp per row; n >= 2048: a 256-thread block per row."""
     K, dt = oracle.PRECS[prec]
-    m, n = 37, 1029
+    m = 37
     A = inputs.mp_uniform(5, (m, n), K, dt)
     x = inputs.mp_uniform(6, n, K, dt, stream=inputs.STREAM_X)
     g = host(mp.gemv(prec, dev(A), dev(x)))
