@@ -99,9 +99,9 @@ def test_dot_workspace_errors(mp):
 
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "tf"])
-@pytest.mark.parametrize("n", [1029, 2500])
+@pytest.mark.parametrize("n", [600, 1029, 2500, 5000])
 def test_gemv_within_bound(mp, oracle, prec, n):
-    """n < 2048: a warp per row; n >= 2048: a 256-thread block per row."""
+    """37 rows: n = 600, 1029, 2500, 5000 run 32, 64, 128, 256 threads per row."""
     K, dt = oracle.PRECS[prec]
     m = 37
     A = inputs.mp_uniform(5, (m, n), K, dt)
