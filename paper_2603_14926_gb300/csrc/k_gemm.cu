@@ -42,8 +42,39 @@ struct GemmCfg {
 
 constexpr int64_t GEMM_GROUP = 16;  // tile rows per group of the block order
 
-template <class P, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
+// The hybrid engine's rare way out: a thread whose integer path left its domain
+// (failed()) recomputes its own outputs with the FP64 pipe, reading op(A) and
+// op(B) from global memory in the same fold order, so its bits are the FP64
+// sequence's.  Never taken on data whose components stay far from the binary64
+// range limits.
+template <class P, int TM, int TN, int NTX, int NTY>
+__device__ __noinline__ void gemm_fixup(int opA, int opB, int64_t k, const typename P::T *__restrict__ A, int64_t lda,
+                                        int64_t pA, const typename P::T *__restrict__ B, int64_t ldb, int64_t pB,
+                                        int64_t i0, int64_t j0, int ty, int tx, int64_t m, int64_t n,
+                                        typename P::T *__restrict__ C, int64_t ldc, int64_t pC)
+{
+    using T = typename P::T;
+    using V = typename P::V;
+    NativeEngine<T> nat;
+    for (int r = 0; r < TM; r++) {
+        const int64_t gi = i0 + ty + r * NTY;
+        if (gi >= m) continue;
+        for (int q = 0; q < TN; q++) {
+            const int64_t gj = j0 + tx + q * NTX;
+            if (gj >= n) continue;
+            V acc = vzero<P>();
+            for (int64_t l = 0; l < k; l++) {
+                const V a = vload<P>(A, pA, opA == 0 ? gi * lda + l : l * lda + gi);
+                const V b = vload<P>(B, pB, opB == 0 ? l * ldb + gj : gj * ldb + l);
+                acc = P::add(acc, P::mul(a, b, nat), nat);
+            }
+            vstore<P>(C, pC, gi * ldc + gj, acc);
+        }
+    }
+}
+
+template <class P, class E, int MINB, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT, MINB)
     k_gemm(int opA, int opB, int64_t m, int64_t n, int64_t k, const typename P::T *__restrict__ A,
            int64_t lda, int64_t pA, const typename P::T *__restrict__ B, int64_t ldb, int64_t pB,
            typename P::T *__restrict__ C, int64_t ldc, int64_t pC)
@@ -66,6 +97,7 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
     const int64_t i0 = (first + r_in % rows) * BM, j0 = (r_in / rows) * BN;
 
     V acc[TM][TN];
+    E eng;
 #pragma unroll
     for (int r = 0; r < TM; r++)
 #pragma unroll
@@ -107,9 +139,13 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
 #pragma unroll
             for (int r = 0; r < TM; r++)
 #pragma unroll
-                for (int s = 0; s < TN; s++) acc[r][s] = P::add(acc[r][s], P::mul(a[r], b[s]));
+                for (int s = 0; s < TN; s++) acc[r][s] = P::add(acc[r][s], P::mul(a[r], b[s], eng), eng);
         }
         __syncthreads();
+    }
+    if (eng.failed()) {
+        gemm_fixup<P, TM, TN, G::NTX, G::NTY>(opA, opB, k, A, lda, pA, B, ldb, pB, i0, j0, ty, tx, m, n, C, ldc, pC);
+        return;
     }
 #pragma unroll
     for (int r = 0; r < TM; r++) {
@@ -123,7 +159,7 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
     }
 }
 
-template <class P, int BM, int BN, int BK, int TM, int TN>
+template <class P, class E, int MINB, int BM, int BN, int BK, int TM, int TN>
 static mp_status gemm_run(int opA, int opB, int64_t m, int64_t n, int64_t k, const typename P::T *A,
                           int64_t lda, int64_t pA, const typename P::T *B, int64_t ldb, int64_t pB,
                           typename P::T *C, int64_t ldc, int64_t pC, cudaStream_t s)
@@ -132,8 +168,8 @@ static mp_status gemm_run(int opA, int opB, int64_t m, int64_t n, int64_t k, con
     const int64_t gx = (n + BN - 1) / BN, gy = (m + BM - 1) / BM;
     if (gx * gy > 0x7fffffff) return MP_EINVAL;
     dim3 grid((unsigned)(gx * gy));
-    k_gemm<P, BM, BN, BK, TM, TN><<<grid, G::NT, 0, s>>>(opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C,
-                                                          ldc, pC);
+    k_gemm<P, E, MINB, BM, BN, BK, TM, TN><<<grid, G::NT, 0, s>>>(opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C,
+                                                                   ldc, pC);
     return launch_status();
 }
 
@@ -196,10 +232,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-template <class P, int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
+template <class P, class E, int MINB, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT, MINB)
     k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int opA, int opB,
-               int64_t m, int64_t n, int64_t k, typename P::T *__restrict__ C, int64_t ldc, int64_t pC)
+               int64_t m, int64_t n, int64_t k, const typename P::T *__restrict__ A, int64_t lda, int64_t pA,
+               const typename P::T *__restrict__ B, int64_t ldb, int64_t pB, typename P::T *__restrict__ C,
+               int64_t ldc, int64_t pC)
 {
     using T = typename P::T;
     using V = typename P::V;
@@ -244,6 +282,7 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
     }
 
     V acc[TM][TN];
+    E eng;
 #pragma unroll
     for (int r = 0; r < TM; r++)
 #pragma unroll
@@ -282,10 +321,14 @@ __global__ void __launch_bounds__(GemmCfg<P, BM, BN, BK, TM, TN>::NT)
 #pragma unroll
             for (int r = 0; r < TM; r++)
 #pragma unroll
-                for (int q = 0; q < TN; q++) acc[r][q] = P::add(acc[r][q], P::mul(a[r], b[q]));
+                for (int q = 0; q < TN; q++) acc[r][q] = P::add(acc[r][q], P::mul(a[r], b[q], eng), eng);
         }
         __syncthreads();  // every read of stage s is done before it is refilled
         if (tid == 0 && t + 2 < ktiles) issue(t + 2, s);
+    }
+    if (eng.failed()) {
+        gemm_fixup<P, TM, TN, G::NTX, G::NTY>(opA, opB, k, A, lda, pA, B, ldb, pB, i0, j0, ty, tx, m, n, C, ldc, pC);
+        return;
     }
 #pragma unroll
     for (int r = 0; r < TM; r++) {
@@ -338,7 +381,7 @@ static bool make_tensor_map(CUtensorMap *map, const typename P::T *ptr, int64_t 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <class P, int BM, int BN, int BK, int TM, int TN>
+template <class P, class E, int MINB, int BM, int BN, int BK, int TM, int TN>
 static mp_status gemm_run_tma(int opA, int opB, int64_t m, int64_t n, int64_t k, const typename P::T *A, int64_t lda,
                               int64_t pA, const typename P::T *B, int64_t ldb, int64_t pB, typename P::T *C, int64_t ldc,
                               int64_t pC, cudaStream_t s)
@@ -351,14 +394,15 @@ static mp_status gemm_run_tma(int opA, int opB, int64_t m, int64_t n, int64_t k,
                     (opB == 0 ? make_tensor_map<P>(&mb, B, n, k, ldb, pB, BN, BK)
                               : make_tensor_map<P>(&mb, B, k, n, ldb, pB, BK, BN));
     if (!ok)  // layout outside TMA's rules: the plain kernel computes the same bits
-        return gemm_run<P, BM, BN, BK, TM, TN>(opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C, ldc, pC, s);
+        return gemm_run<P, E, MINB, BM, BN, BK, TM, TN>(opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C, ldc, pC, s);
     const int64_t gx = (n + BN - 1) / BN, gy = (m + BM - 1) / BM;
     if (gx * gy > 0x7fffffff) return MP_EINVAL;
     const size_t smem = 2 * (size_t)P::K * (BM * BK + BK * BN) * sizeof(T) + 2 * sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<P, BM, BN, BK, TM, TN>,
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tma<P, E, MINB, BM, BN, BK, TM, TN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    k_gemm_tma<P, BM, BN, BK, TM, TN><<<(unsigned)(gx * gy), G::NT, smem, s>>>(ma, mb, opA, opB, m, n, k, C, ldc, pC);
+    k_gemm_tma<P, E, MINB, BM, BN, BK, TM, TN><<<(unsigned)(gx * gy), G::NT, smem, s>>>(
+        ma, mb, opA, opB, m, n, k, A, lda, pA, B, ldb, pB, C, ldc, pC);
     return launch_status();
 }
 
@@ -370,7 +414,10 @@ static mp_status gemm_run_tma(int opA, int opB, int64_t m, int64_t n, int64_t k,
 template <class P, bool F64 = P::fp64> struct GemmTable;
 
 template <class P> struct GemmTable<P, true> {
-    static constexpr int count = 5;
+    using N = NativeEngine<double>;
+    using H = HybridEngine<false>;
+    using HQ = HybridEngine<true>;
+    static constexpr int count = 9;
     static const char *name(int c)
     {
         switch (c) {
@@ -379,23 +426,32 @@ template <class P> struct GemmTable<P, true> {
         case 2: return "BM32 BN64 BK8 TM2 TN4 (256 thr)";
         case 3: return "BM16 BN32 BK16 TM1 TN2 (256 thr)";
         case 4: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA-staged double buffer";
+        case 5: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum (integer error term)";
+        case 6: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum + QuickTwoSum";
+        case 7: return "BM32 BN32 BK16 TM2 TN2 (256 thr), hybrid TwoSum";
+        case 8: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum, 1 block/SM register budget";
         }
         return nullptr;
     }
-    static constexpr int fallback = 4;  // configuration used for config = -1
+    static constexpr int fallback = 5;  // configuration used for config = -1
     template <typename... Args> static mp_status run(int c, Args... a)
     {
         switch (c) {
-        case 1: return gemm_run<P, 16, 16, 16, 1, 1>(a...);
-        case 2: return gemm_run<P, 32, 64, 8, 2, 4>(a...);
-        case 3: return gemm_run<P, 16, 32, 16, 1, 2>(a...);
-        case 4: return gemm_run_tma<P, 32, 32, 16, 2, 2>(a...);
-        default: return gemm_run<P, 32, 32, 16, 2, 2>(a...);
+        case 1: return gemm_run<P, N, 2, 16, 16, 16, 1, 1>(a...);
+        case 2: return gemm_run<P, N, 1, 32, 64, 8, 2, 4>(a...);
+        case 3: return gemm_run<P, N, 2, 16, 32, 16, 1, 2>(a...);
+        case 4: return gemm_run_tma<P, N, 2, 32, 32, 16, 2, 2>(a...);
+        case 5: return gemm_run_tma<P, H, 2, 32, 32, 16, 2, 2>(a...);
+        case 6: return gemm_run_tma<P, HQ, 2, 32, 32, 16, 2, 2>(a...);
+        case 7: return gemm_run<P, H, 2, 32, 32, 16, 2, 2>(a...);
+        case 8: return gemm_run_tma<P, H, 1, 32, 32, 16, 2, 2>(a...);
+        default: return gemm_run<P, N, 2, 32, 32, 16, 2, 2>(a...);
         }
     }
 };
 
 template <class P> struct GemmTable<P, false> {
+    using N = NativeEngine<float>;
     static constexpr int count = 5;
     static const char *name(int c)
     {
@@ -412,11 +468,11 @@ template <class P> struct GemmTable<P, false> {
     template <typename... Args> static mp_status run(int c, Args... a)
     {
         switch (c) {
-        case 1: return gemm_run<P, 64, 64, 16, 4, 4>(a...);
-        case 2: return gemm_run<P, 64, 32, 16, 4, 2>(a...);
-        case 3: return gemm_run<P, 128, 64, 8, 8, 4>(a...);
-        case 4: return gemm_run_tma<P, 32, 32, 16, 2, 2>(a...);
-        default: return gemm_run<P, 32, 32, 16, 2, 2>(a...);
+        case 1: return gemm_run<P, N, 1, 64, 64, 16, 4, 4>(a...);
+        case 2: return gemm_run<P, N, 1, 64, 32, 16, 4, 2>(a...);
+        case 3: return gemm_run<P, N, 1, 128, 64, 8, 8, 4>(a...);
+        case 4: return gemm_run_tma<P, N, 1, 32, 32, 16, 2, 2>(a...);
+        default: return gemm_run<P, N, 1, 32, 32, 16, 2, 2>(a...);
         }
     }
 };

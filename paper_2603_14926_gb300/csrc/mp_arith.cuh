@@ -16,6 +16,8 @@
 #pragma once
 #include <cstdint>
 
+#include "mp_eft_int.cuh"
+
 namespace mp {
 
 template <typename T> struct fpu;
@@ -71,6 +73,61 @@ __device__ __forceinline__ void two_prod(T a, T b, T &p, T &e)
     p = p_;
 }
 
+// ---------------------------------------------------------------------------
+// Engines.  The multicomponent algorithms below are written once against an
+// engine that supplies Algorithms 1-3 and the plain add and multiply; the
+// engine decides which pipe executes them.
+//
+// NativeEngine<T>: every step on the FP64 (or FP32) pipe, as printed.
+// HybridEngine<QTS>: binary64 only.  TwoSum's s from one FP64 add, its error e
+//   from the integer pipes (mp_eft_int.cuh); with QTS also QuickTwoSum's error
+//   where Algorithm 1 is exact (exponent(a) >= exponent(b), or a zero operand).
+//   TwoProd and the plain operations stay on the FP64 pipe.  Outside the
+//   integer path's domain, and for QuickTwoSum outside its exact case, the
+//   engine raises failed(); callers then recompute the result with
+//   NativeEngine, so every output is the FP64 sequence's bits.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct NativeEngine {
+    __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) { mp::two_sum(a, b, s, e); }
+    __device__ __forceinline__ void quick_two_sum(T a, T b, T &s, T &e) { mp::quick_two_sum(a, b, s, e); }
+    __device__ __forceinline__ void two_prod(T a, T b, T &p, T &e) { mp::two_prod(a, b, p, e); }
+    __device__ __forceinline__ T add(T a, T b) { return fpu<T>::add(a, b); }
+    __device__ __forceinline__ T mul(T a, T b) { return fpu<T>::mul(a, b); }
+    __device__ __forceinline__ bool failed() const { return false; }
+};
+
+template <bool QTS> struct HybridEngine {
+    uint32_t bad = 0;
+    __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
+    {
+        const double s_ = __dadd_rn(a, b);
+        e = __longlong_as_double((long long)eft_int::two_sum_err((uint64_t)__double_as_longlong(a),
+                                                                  (uint64_t)__double_as_longlong(b),
+                                                                  (uint64_t)__double_as_longlong(s_), bad));
+        s = s_;
+    }
+    __device__ __forceinline__ void quick_two_sum(double a, double b, double &s, double &e)
+    {
+        if (!QTS) {
+            mp::quick_two_sum(a, b, s, e);
+            return;
+        }
+        const double s_ = __dadd_rn(a, b);
+        const uint64_t A = (uint64_t)__double_as_longlong(a), B = (uint64_t)__double_as_longlong(b);
+        const uint64_t Aa = A & 0x7FFFFFFFFFFFFFFFull, Ba = B & 0x7FFFFFFFFFFFFFFFull;
+        // Algorithm 1 is exact when exponent(a) >= exponent(b) or a = 0; with b = 0 its e is b itself
+        bad |= (uint32_t)!(Aa >= (Ba & 0x7FF0000000000000ull) || Aa == 0 || Ba == 0);
+        const uint64_t E = eft_int::two_sum_err(A, B, (uint64_t)__double_as_longlong(s_), bad);
+        e = __longlong_as_double((long long)(Ba == 0 ? B : E));
+        s = s_;
+    }
+    __device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) { mp::two_prod(a, b, p, e); }
+    __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ bool failed() const { return bad != 0; }
+};
+
 // A K-component number, component 0 leading.  Always held in registers.
 template <typename T, int K> struct mpv {
     T c[K];
@@ -81,49 +138,46 @@ template <typename T, int K> struct mpv {
 // ---------------------------------------------------------------------------
 
 // Algorithm 4 (DWAdd, the sloppy add of the QD library)
-template <typename T>
-__device__ __forceinline__ mpv<T, 2> dw_add_sloppy(const mpv<T, 2> &a, const mpv<T, 2> &b)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 2> dw_add_sloppy(const mpv<T, 2> &a, const mpv<T, 2> &b, E &g)
 {
-    using F = fpu<T>;
     T s, e;
-    two_sum(a.c[0], b.c[0], s, e);
-    e = F::add(e, F::add(a.c[1], b.c[1]));
+    g.two_sum(a.c[0], b.c[0], s, e);
+    e = g.add(e, g.add(a.c[1], b.c[1]));
     mpv<T, 2> r;
-    quick_two_sum(s, e, r.c[0], r.c[1]);
+    g.quick_two_sum(s, e, r.c[0], r.c[1]);
     return r;
 }
 
 // Algorithm 6 (DWBFAdd)
-template <typename T>
-__device__ __forceinline__ mpv<T, 2> dw_add_bf(const mpv<T, 2> &a, const mpv<T, 2> &b)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 2> dw_add_bf(const mpv<T, 2> &a, const mpv<T, 2> &b, E &g)
 {
-    using F = fpu<T>;
     T g1, g1e, g2, g2e, g3, g3e;
-    two_sum(a.c[0], b.c[0], g1, g1e);
-    two_sum(a.c[1], b.c[1], g2, g2e);
-    quick_two_sum(g1, g2, g3, g3e);
-    T g4 = F::add(g1e, g2e);
-    T g5 = F::add(g4, g3e);
+    g.two_sum(a.c[0], b.c[0], g1, g1e);
+    g.two_sum(a.c[1], b.c[1], g2, g2e);
+    g.quick_two_sum(g1, g2, g3, g3e);
+    T g4 = g.add(g1e, g2e);
+    T g5 = g.add(g4, g3e);
     mpv<T, 2> r;
-    quick_two_sum(g3, g5, r.c[0], r.c[1]);
+    g.quick_two_sum(g3, g5, r.c[0], r.c[1]);
     return r;
 }
 
 // Algorithm 7 (DWMul; its undefined "QuickTwoProd" read as QuickTwoSum) and
 // Algorithm 8 (DWBFMul) are the same operation sequence:
 // (p00, pe00) = TwoProd(a0, b0); g1 = a0*b1 + a1*b0; g2 = pe00 + g1; QuickTwoSum(p00, g2).
-template <typename T>
-__device__ __forceinline__ mpv<T, 2> dw_mul_bf(const mpv<T, 2> &a, const mpv<T, 2> &b)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 2> dw_mul_bf(const mpv<T, 2> &a, const mpv<T, 2> &b, E &g)
 {
-    using F = fpu<T>;
     T p00, pe00;
-    two_prod(a.c[0], b.c[0], p00, pe00);
-    T p01 = F::mul(a.c[0], b.c[1]);
-    T p10 = F::mul(a.c[1], b.c[0]);
-    T g1 = F::add(p01, p10);
-    T g2 = F::add(pe00, g1);
+    g.two_prod(a.c[0], b.c[0], p00, pe00);
+    T p01 = g.mul(a.c[0], b.c[1]);
+    T p10 = g.mul(a.c[1], b.c[0]);
+    T g1 = g.add(p01, p10);
+    T g2 = g.add(pe00, g1);
     mpv<T, 2> r;
-    quick_two_sum(p00, g2, r.c[0], r.c[1]);
+    g.quick_two_sum(p00, g2, r.c[0], r.c[1]);
     return r;
 }
 
@@ -132,54 +186,52 @@ __device__ __forceinline__ mpv<T, 2> dw_mul_bf(const mpv<T, 2> &a, const mpv<T, 
 // ---------------------------------------------------------------------------
 
 // Algorithm 11 (TWBFAdd)
-template <typename T>
-__device__ __forceinline__ mpv<T, 3> tw_add_bf(const mpv<T, 3> &A, const mpv<T, 3> &B)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 3> tw_add_bf(const mpv<T, 3> &A, const mpv<T, 3> &B, E &g)
 {
-    using F = fpu<T>;
     T a1, b1, c1, d1, e1, f1, a2, c2, d2, e2, a3, d3, b3, c3, c5, d5, b6, c6, b7;
     mpv<T, 3> r;
-    two_sum(A.c[0], B.c[0], a1, b1);
-    two_sum(A.c[1], B.c[1], c1, d1);
-    two_sum(A.c[2], B.c[2], e1, f1);
-    quick_two_sum(a1, c1, a2, c2);
-    T b2 = F::add(b1, f1);
-    two_sum(d1, e1, d2, e2);
-    quick_two_sum(a2, d2, a3, d3);
-    two_sum(b2, c2, b3, c3);
-    T c4 = F::add(c3, e2);
-    two_sum(c4, d3, c5, d5);
-    two_sum(b3, c5, b6, c6);
-    quick_two_sum(a3, b6, r.c[0], b7);
-    T c7 = F::add(c6, d5);
-    quick_two_sum(b7, c7, r.c[1], r.c[2]);
+    g.two_sum(A.c[0], B.c[0], a1, b1);
+    g.two_sum(A.c[1], B.c[1], c1, d1);
+    g.two_sum(A.c[2], B.c[2], e1, f1);
+    g.quick_two_sum(a1, c1, a2, c2);
+    T b2 = g.add(b1, f1);
+    g.two_sum(d1, e1, d2, e2);
+    g.quick_two_sum(a2, d2, a3, d3);
+    g.two_sum(b2, c2, b3, c3);
+    T c4 = g.add(c3, e2);
+    g.two_sum(c4, d3, c5, d5);
+    g.two_sum(b3, c5, b6, c6);
+    g.quick_two_sum(a3, b6, r.c[0], b7);
+    T c7 = g.add(c6, d5);
+    g.quick_two_sum(b7, c7, r.c[1], r.c[2]);
     return r;
 }
 
 // Algorithm 12 (TWBFMul)
-template <typename T>
-__device__ __forceinline__ mpv<T, 3> tw_mul_bf(const mpv<T, 3> &A, const mpv<T, 3> &B)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 3> tw_mul_bf(const mpv<T, 3> &A, const mpv<T, 3> &B, E &g)
 {
-    using F = fpu<T>;
     T a0, b0, c0, e0, d0, f0, c1, d1, b2, c2, a3, b3, b5, c5, b6;
     mpv<T, 3> r;
-    two_prod(A.c[0], B.c[0], a0, b0);
-    two_prod(A.c[0], B.c[1], c0, e0);
-    two_prod(A.c[1], B.c[0], d0, f0);
-    T g0 = F::mul(A.c[0], B.c[2]);
-    T h0 = F::mul(A.c[1], B.c[1]);
-    T i0 = F::mul(A.c[2], B.c[0]);
-    two_sum(c0, d0, c1, d1);
-    T e1 = F::add(e0, f0);
-    T g1 = F::add(g0, i0);
-    two_sum(b0, c1, b2, c2);
-    T g2 = F::add(g1, h0);
-    quick_two_sum(a0, b2, a3, b3);
-    T c3 = F::add(c2, d1);
-    T e3 = F::add(e1, g2);
-    T c4 = F::add(c3, e3);
-    quick_two_sum(b3, c4, b5, c5);
-    quick_two_sum(a3, b5, r.c[0], b6);
-    quick_two_sum(b6, c5, r.c[1], r.c[2]);
+    g.two_prod(A.c[0], B.c[0], a0, b0);
+    g.two_prod(A.c[0], B.c[1], c0, e0);
+    g.two_prod(A.c[1], B.c[0], d0, f0);
+    T g0 = g.mul(A.c[0], B.c[2]);
+    T h0 = g.mul(A.c[1], B.c[1]);
+    T i0 = g.mul(A.c[2], B.c[0]);
+    g.two_sum(c0, d0, c1, d1);
+    T e1 = g.add(e0, f0);
+    T g1 = g.add(g0, i0);
+    g.two_sum(b0, c1, b2, c2);
+    T g2 = g.add(g1, h0);
+    g.quick_two_sum(a0, b2, a3, b3);
+    T c3 = g.add(c2, d1);
+    T e3 = g.add(e1, g2);
+    T c4 = g.add(c3, e3);
+    g.quick_two_sum(b3, c4, b5, c5);
+    g.quick_two_sum(a3, b5, r.c[0], b6);
+    g.quick_two_sum(b6, c5, r.c[1], r.c[2]);
     return r;
 }
 
@@ -188,87 +240,85 @@ __device__ __forceinline__ mpv<T, 3> tw_mul_bf(const mpv<T, 3> &A, const mpv<T, 
 // ---------------------------------------------------------------------------
 
 // Algorithm 13 (QWBFAdd)
-template <typename T>
-__device__ __forceinline__ mpv<T, 4> qw_add_bf(const mpv<T, 4> &A, const mpv<T, 4> &B)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 4> qw_add_bf(const mpv<T, 4> &A, const mpv<T, 4> &B, E &g)
 {
-    using F = fpu<T>;
     T a1, b1, c1, d1, e1, f1, g1, h1, a2, c2, d2, e2, f2, g2, b3, g3, c3, d3, e3, f3,
         a4, c4, d4, e4, b5, d5, b6, c6, d6, e6, a7, b7, c7, d7, b8, c8, b10, c10, d10, c11;
     mpv<T, 4> r;
-    two_sum(A.c[0], B.c[0], a1, b1);
-    two_sum(A.c[1], B.c[1], c1, d1);
-    two_sum(A.c[2], B.c[2], e1, f1);
-    two_sum(A.c[3], B.c[3], g1, h1);
-    quick_two_sum(a1, c1, a2, c2);
-    T b2 = F::add(b1, h1);
-    two_sum(d1, e1, d2, e2);
-    two_sum(f1, g1, f2, g2);
-    two_sum(b2, g2, b3, g3);
-    quick_two_sum(c2, d2, c3, d3);
-    two_sum(e2, f2, e3, f3);
-    quick_two_sum(a2, c3, a4, c4);
-    quick_two_sum(d3, e3, d4, e4);
-    two_sum(b3, d4, b5, d5);
-    T e5 = F::add(e4, f3);
-    two_sum(b5, c4, b6, c6);
-    two_sum(d5, e5, d6, e6);
-    quick_two_sum(a4, b6, a7, b7);
-    quick_two_sum(c6, d6, c7, d7);
-    T e8 = F::add(e6, g3);
-    quick_two_sum(b7, c7, b8, c8);
-    T d9 = F::add(d7, e8);
-    quick_two_sum(a7, b8, r.c[0], b10);
-    quick_two_sum(c8, d9, c10, d10);
-    quick_two_sum(b10, c10, r.c[1], c11);
-    quick_two_sum(c11, d10, r.c[2], r.c[3]);
+    g.two_sum(A.c[0], B.c[0], a1, b1);
+    g.two_sum(A.c[1], B.c[1], c1, d1);
+    g.two_sum(A.c[2], B.c[2], e1, f1);
+    g.two_sum(A.c[3], B.c[3], g1, h1);
+    g.quick_two_sum(a1, c1, a2, c2);
+    T b2 = g.add(b1, h1);
+    g.two_sum(d1, e1, d2, e2);
+    g.two_sum(f1, g1, f2, g2);
+    g.two_sum(b2, g2, b3, g3);
+    g.quick_two_sum(c2, d2, c3, d3);
+    g.two_sum(e2, f2, e3, f3);
+    g.quick_two_sum(a2, c3, a4, c4);
+    g.quick_two_sum(d3, e3, d4, e4);
+    g.two_sum(b3, d4, b5, d5);
+    T e5 = g.add(e4, f3);
+    g.two_sum(b5, c4, b6, c6);
+    g.two_sum(d5, e5, d6, e6);
+    g.quick_two_sum(a4, b6, a7, b7);
+    g.quick_two_sum(c6, d6, c7, d7);
+    T e8 = g.add(e6, g3);
+    g.quick_two_sum(b7, c7, b8, c8);
+    T d9 = g.add(d7, e8);
+    g.quick_two_sum(a7, b8, r.c[0], b10);
+    g.quick_two_sum(c8, d9, c10, d10);
+    g.quick_two_sum(b10, c10, r.c[1], c11);
+    g.quick_two_sum(c11, d10, r.c[2], r.c[3]);
     return r;
 }
 
 // Algorithm 14 (QDBFMul)
-template <typename T>
-__device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 4> &B)
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 4> &B, E &g)
 {
-    using F = fpu<T>;
     T a0, b0, c0, e0, d0, f0, g0, j0, h0, k0, i0, l0, c1, d1, e1, f1, g1, i1, b2, c2, e2, h2,
         a3, b3, c3, d3, e3, g3, c4, e4, c6, d6, b7, c7, b8, c8, d8, c9;
     mpv<T, 4> r;
-    two_prod(A.c[0], B.c[0], a0, b0);
-    two_prod(A.c[0], B.c[1], c0, e0);
-    two_prod(A.c[1], B.c[0], d0, f0);
-    two_prod(A.c[0], B.c[2], g0, j0);
-    two_prod(A.c[1], B.c[1], h0, k0);
-    two_prod(A.c[2], B.c[0], i0, l0);
-    T m0 = F::mul(A.c[0], B.c[3]);
-    T n0 = F::mul(A.c[1], B.c[2]);
-    T o0 = F::mul(A.c[2], B.c[1]);
-    T p0 = F::mul(A.c[3], B.c[0]);
-    two_sum(c0, d0, c1, d1);
-    two_sum(e0, f0, e1, f1);
-    two_sum(g0, i0, g1, i1);
-    T j1 = F::add(j0, l0);
-    T m1 = F::add(m0, p0);
-    T n1 = F::add(n0, o0);
-    two_sum(b0, c1, b2, c2);
-    two_sum(e1, h0, e2, h2);
-    T f2 = F::add(f1, j1);
-    T i2 = F::add(i1, k0);
-    T m2 = F::add(m1, n1);
-    quick_two_sum(a0, b2, a3, b3);
-    quick_two_sum(c2, d1, c3, d3);
-    two_sum(e2, g1, e3, g3);
-    T f3 = F::add(f2, m2);
-    T h3 = F::add(h2, i2);
-    two_sum(c3, e3, c4, e4);
-    T d4 = F::add(d3, h3);
-    T f4 = F::add(f3, g3);
-    T d5 = F::add(d4, e4);
-    two_sum(c4, d5, c6, d6);
-    two_sum(b3, c6, b7, c7);
-    T d7 = F::add(d6, f4);
-    quick_two_sum(a3, b7, r.c[0], b8);
-    two_sum(c7, d7, c8, d8);
-    two_sum(b8, c8, r.c[1], c9);
-    quick_two_sum(c9, d8, r.c[2], r.c[3]);
+    g.two_prod(A.c[0], B.c[0], a0, b0);
+    g.two_prod(A.c[0], B.c[1], c0, e0);
+    g.two_prod(A.c[1], B.c[0], d0, f0);
+    g.two_prod(A.c[0], B.c[2], g0, j0);
+    g.two_prod(A.c[1], B.c[1], h0, k0);
+    g.two_prod(A.c[2], B.c[0], i0, l0);
+    T m0 = g.mul(A.c[0], B.c[3]);
+    T n0 = g.mul(A.c[1], B.c[2]);
+    T o0 = g.mul(A.c[2], B.c[1]);
+    T p0 = g.mul(A.c[3], B.c[0]);
+    g.two_sum(c0, d0, c1, d1);
+    g.two_sum(e0, f0, e1, f1);
+    g.two_sum(g0, i0, g1, i1);
+    T j1 = g.add(j0, l0);
+    T m1 = g.add(m0, p0);
+    T n1 = g.add(n0, o0);
+    g.two_sum(b0, c1, b2, c2);
+    g.two_sum(e1, h0, e2, h2);
+    T f2 = g.add(f1, j1);
+    T i2 = g.add(i1, k0);
+    T m2 = g.add(m1, n1);
+    g.quick_two_sum(a0, b2, a3, b3);
+    g.quick_two_sum(c2, d1, c3, d3);
+    g.two_sum(e2, g1, e3, g3);
+    T f3 = g.add(f2, m2);
+    T h3 = g.add(h2, i2);
+    g.two_sum(c3, e3, c4, e4);
+    T d4 = g.add(d3, h3);
+    T f4 = g.add(f3, g3);
+    T d5 = g.add(d4, e4);
+    g.two_sum(c4, d5, c6, d6);
+    g.two_sum(b3, c6, b7, c7);
+    T d7 = g.add(d6, f4);
+    g.quick_two_sum(a3, b7, r.c[0], b8);
+    g.two_sum(c7, d7, c8, d8);
+    g.two_sum(b8, c8, r.c[1], c9);
+    g.quick_two_sum(c9, d8, r.c[2], r.c[3]);
     return r;
 }
 
@@ -283,8 +333,24 @@ __device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 
         static constexpr int newton_steps = NEWTON;                                         \
         static constexpr bool fp64 = FP64PIPE;                                              \
         using V = mpv<TYPE, KK>;                                                            \
-        static __device__ __forceinline__ V add(const V &a, const V &b) { return ADDF(a, b); } \
-        static __device__ __forceinline__ V mul(const V &a, const V &b) { return MULF(a, b); } \
+        template <class E> static __device__ __forceinline__ V add(const V &a, const V &b, E &g) \
+        {                                                                                   \
+            return ADDF(a, b, g);                                                           \
+        }                                                                                   \
+        template <class E> static __device__ __forceinline__ V mul(const V &a, const V &b, E &g) \
+        {                                                                                   \
+            return MULF(a, b, g);                                                           \
+        }                                                                                   \
+        static __device__ __forceinline__ V add(const V &a, const V &b)                     \
+        {                                                                                   \
+            NativeEngine<TYPE> g;                                                           \
+            return ADDF(a, b, g);                                                           \
+        }                                                                                   \
+        static __device__ __forceinline__ V mul(const V &a, const V &b)                     \
+        {                                                                                   \
+            NativeEngine<TYPE> g;                                                           \
+            return MULF(a, b, g);                                                           \
+        }                                                                                   \
     };
 
 MP_PREC_TAG(P_dd, double, 2, dw_add_bf<double>, dw_mul_bf<double>, 2, true)

@@ -1,0 +1,121 @@
+// mp_eft_int.cuh -- the error term of TwoSum (Algorithm 2) computed exactly on the
+// integer pipes, for binary64.
+//
+// TwoSum returns s = fl(a + b) and e = a + b - s, which is exactly representable
+// (Section 2, Algorithms 1-2).  On this GPU the FP64 pipe retires about 2 lanes per
+// clock per SM while the integer ALU and FMA pipes retire 64 each, so instead of
+// the five further FP64 operations of Algorithm 2 the engine takes s from one FP64
+// add and evaluates e = a + b - s in integer arithmetic:
+//
+//   every finite binary64 x with biased exponent E and fraction f is m * 2^(E' - 1075)
+//   with E' = max(E, 1) and m = f + 2^52 [E > 0] (IEEE 754 binary64 encoding), so
+//
+//   e * 2^(1075 - u) = ma 2^(Ea' - u) + mb 2^(Eb' - u) - ms 2^(Es' - u),  u = min(Ea', Eb', Es'),
+//
+// with signs applied.  |e| <= ulp(s)/2 and e is a multiple of the smallest unit in
+// play, so the right-hand side is an integer below 2^55 in magnitude: it can be
+// evaluated modulo 2^64 (terms shifted by 64 or more vanish) and read back as a
+// signed 64-bit value, then normalised and packed.  The result is bit-identical to
+// the FP64 sequence of Algorithm 2 (+0 when the sum is exact) whenever
+//   - a and b are finite with biased exponent <= 2045 (no intermediate of
+//     Algorithm 2 can overflow), and
+//   - e is zero or normal.
+// Outside that domain the function raises `bad`; callers then recompute the whole
+// result with the FP64 pipe, so every output stays exactly the paper's operation
+// sequence.
+//
+// The functions are also compiled for the host, where a unit test checks them
+// against the host's binary64 arithmetic.
+#pragma once
+#include <cstdint>
+
+#define MP_HD __host__ __device__ __forceinline__
+
+namespace mp {
+namespace eft_int {
+
+MP_HD uint32_t lo32(uint64_t x) { return (uint32_t)x; }
+MP_HD uint32_t hi32(uint64_t x) { return (uint32_t)(x >> 32); }
+MP_HD uint64_t mk64(uint32_t h, uint32_t l) { return ((uint64_t)h << 32) | l; }
+MP_HD int imin(int a, int b) { return a < b ? a : b; }
+
+// 1 << k as a 32-bit word, 0 when k >= 32 (PTX clamps the shift count).
+MP_HD uint32_t pow2_32(uint32_t k)
+{
+#ifdef __CUDA_ARCH__
+    uint32_t r;
+    asm("shl.b32 %0, 1, %1;" : "=r"(r) : "r"(k));
+    return r;
+#else
+    return k < 32 ? 1u << k : 0u;
+#endif
+}
+
+MP_HD int clz64(uint64_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// low word of (hi:lo) >> 11
+MP_HD uint32_t shr11_lo(uint32_t lo, uint32_t hi)
+{
+#ifdef __CUDA_ARCH__
+    return __funnelshift_r(lo, hi, 11);
+#else
+    return (lo >> 11) | (hi << 21);
+#endif
+}
+
+// m * 2^k mod 2^64 for any k >= 0, as multiplications (FMA pipe) by 2^k.
+MP_HD uint64_t shl_mod(uint64_t m, uint32_t k)
+{
+    const uint32_t plo = pow2_32(k), phi = pow2_32(k - 32u);  // k - 32 wraps to a huge count when k < 32
+    const uint64_t r = (uint64_t)lo32(m) * plo;
+    return mk64(hi32(r) + hi32(m) * plo + lo32(m) * phi, lo32(r));
+}
+
+// Biased exponent clamped to >= 1, and the integer significand (hidden bit only
+// for E > 0), of the binary64 pattern x.
+MP_HD void unpack(uint64_t x, int &e1, uint64_t &m)
+{
+    const uint32_t h = hi32(x);
+    const int e = (int)((h >> 20) & 0x7FFu);
+    e1 = e > 0 ? e : 1;
+    m = mk64((h & 0xFFFFFu) | (e > 0 ? 0x100000u : 0u), lo32(x));
+}
+
+// e = a + b - s for s = fl(a + b), as a binary64 pattern.  `bad` is raised when
+// the operands leave the domain stated above.
+MP_HD uint64_t two_sum_err(uint64_t A, uint64_t B, uint64_t S, uint32_t &bad)
+{
+    int ea, eb, es;
+    uint64_t ma, mb, ms;
+    unpack(A, ea, ma);
+    unpack(B, eb, mb);
+    unpack(S, es, ms);
+    const int u = imin(imin(ea, eb), es);
+    uint64_t ta = shl_mod(ma, (uint32_t)(ea - u)), tb = shl_mod(mb, (uint32_t)(eb - u));
+    const uint64_t ts = shl_mod(ms, (uint32_t)(es - u));
+    // conditional negation by the sign words: (t ^ k) - k with k = 0 or all ones
+    const uint64_t ka = (uint64_t)((int64_t)A >> 63), kb = (uint64_t)((int64_t)B >> 63),
+                   ks = (uint64_t)((int64_t)S >> 63);
+    ta = (ta ^ ka) - ka;
+    tb = (tb ^ kb) - kb;
+    const uint64_t ei = ta + tb - ((ts ^ ks) - ks);
+    const uint64_t kn = (uint64_t)((int64_t)ei >> 63);
+    const uint64_t mag = (ei ^ kn) - kn;
+    const int lz = clz64(mag);
+    const uint64_t norm = shl_mod(mag, (uint32_t)lz & 63u);  // leading one at bit 63
+    const int be = 11 - lz + u;                               // biased exponent of e
+    const uint32_t eh = ((hi32(norm) >> 11) + ((uint32_t)(be - 1) << 20)) | (hi32(kn) & 0x80000000u);
+    const uint32_t el = shr11_lo(lo32(norm), hi32(norm));
+    bad |= (uint32_t)(ea > 2045) | (uint32_t)(eb > 2045) | (uint32_t)(es > 2046) | (uint32_t)(mag != 0 && be < 1);
+    return mag == 0 ? 0 : mk64(eh, el);
+}
+
+}  // namespace eft_int
+}  // namespace mp
