@@ -41,6 +41,11 @@ import numpy as np  # noqa: E402
 INSTR_MUL = {"dd": 9, "ddc": 9, "td": 39, "qd": 106, "ds": 9, "tf": 39, "qf": 106}
 INSTR_ADD = {"dd": 20, "ddc": 11, "td": 57, "qd": 103, "ds": 20, "tf": 57, "qf": 103}
 FMA_PER_MUL = {"dd": 1, "ddc": 1, "td": 3, "qd": 6, "ds": 1, "tf": 3, "qf": 6}
+# TwoSum (Algorithm 2) calls per multiply-add: add + multiply.  The hybrid engine
+# issues one FP64 add for each instead of six and takes the error term from the
+# integer pipes, so a hybrid multiply-add issues mac_instr - 5 * TWO_SUMS FP64
+# instructions.
+TWO_SUMS = {"dd": 2, "ddc": 1, "td": 9, "qd": 22}
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 dense FP64, FMA = 2 flops
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SM_MAX_MHZ = 2070.0
@@ -48,6 +53,11 @@ SM_MAX_MHZ = 2070.0
 
 def mac_instr(prec):
     return INSTR_MUL[prec] + INSTR_ADD[prec]
+
+
+def mac_instr_hybrid(prec):
+    """FP64-pipe instructions of one multiply-add under the hybrid engine."""
+    return mac_instr(prec) - 5 * TWO_SUMS.get(prec, 0)
 
 
 # ---------------------------------------------------------------------------
@@ -257,9 +267,13 @@ def time_region(fn, steps, world, stream):
     return total, launches
 
 
-def gemm_traffic(prec, n):
+def gemm_profile_name(prec, n, hybrid):
+    return f"k_gemm_{'hybrid_' if hybrid else ''}{prec}_{n}.md"
+
+
+def gemm_traffic(prec, n, hybrid):
     """DRAM bytes per launch recorded by ncu for this kernel and size, if any."""
-    path = os.path.join(ROOT, "profiles", f"k_gemm_{prec}_{n}.md")
+    path = os.path.join(ROOT, "profiles", gemm_profile_name(prec, n, hybrid))
     try:
         for line in open(path):
             if line.startswith("traffic_bytes_per_launch:"):
@@ -610,19 +624,29 @@ def run_gpu(a, rank, world, pool):
     ms_step = total / a.steps * 1e3
     value = job_throughput(world, a.steps, 2.0 * n ** 3, total)
     launch_s = statistics.mean(per_launch)
-    instr = n ** 3 * mac_instr(prec)
+    from paper_2603_14926_gb300.tune import best_gemm_config
+
+    cfg = best_gemm_config(prec, n, n, n)  # -1: the built-in choice, the hybrid engine for binary64
+    hybrid = prec in TWO_SUMS and (cfg < 0 or "hybrid" in mpg.gemm_config_name(prec, cfg))
+    instr = n ** 3 * (mac_instr_hybrid(prec) if hybrid else mac_instr(prec))
     peak_nominal = NOMINAL_FP64_TFLOPS * 1e12 / 2 / 1e9  # G FP64 instructions/s
     achieved = instr / launch_s / 1e9
     peak_live = fp64_peak_live() / 1e9
-    roofline = {"bound": "alu", "kernel": f"k_gemm_tma<P_{prec}, 32, 32, 16, 2, 2> (TMA-staged tiles; FP64 pipe)",
+    kernel = (f"k_gemm_tma<P_{prec}, HybridEngine<false>, 2, 32, 32, 16, 2, 2> (TMA-staged tiles; TwoSum error "
+              f"terms on the integer pipes, every other step on the FP64 pipe)" if hybrid else
+              f"k_gemm_tma<P_{prec}, NativeEngine<double>, 2, 32, 32, 16, 2, 2> (TMA-staged tiles; FP64 pipe)")
+    roofline = {"bound": "alu", "kernel": kernel,
                 "achieved": achieved,
                 "peak": peak_nominal, "unit": "G FP64 instr/s", "frac": achieved / peak_nominal,
                 "peak_source": "nominal 1.25 TFLOP/s FP64 (FMA = 2) -> 625 G FP64 instructions/s "
                                "(152 SMs x 2 lanes/clk x 2.06 GHz)",
                 "peak_measured_live": peak_live, "frac_of_measured": achieved / peak_live,
+                "fp64_instr_per_mac": mac_instr_hybrid(prec) if hybrid else mac_instr(prec),
+                "paper_fp64_instr_per_mac": mac_instr(prec),
+                "paper_sequence_equiv_instr_per_s": n ** 3 * mac_instr(prec) / launch_s / 1e9,
                 "algorithmic_instr_per_launch": instr, "launch_ms": launch_s * 1e3,
-                "traffic": gemm_traffic(prec, n),
-                "traffic_source": "profiles/k_gemm_qd_2048.md (ncu dram__bytes_read.sum + "
+                "traffic": gemm_traffic(prec, n, hybrid),
+                "traffic_source": f"profiles/{gemm_profile_name(prec, n, hybrid)} (ncu dram__bytes_read.sum + "
                                   "dram__bytes_write.sum, one launch of this kernel at this size)",
                 "algorithmic_bytes_per_launch": int(3 * A.nbytes)}
     # end to end through the public API with host-resident inputs

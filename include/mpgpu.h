@@ -133,12 +133,23 @@ const char *mp_version(void);
 /* the result is bit-identical to the CPU oracle.  C must not alias A or B. */
 /* mp_gemm_ex_P selects a tile configuration (0 .. mp_gemm_num_configs_P()-1,*/
 /* or -1 for the built-in choice); configurations differ only in speed.     */
-/* Configuration 4 stages the tiles with TMA (cp.async.bulk.tensor, double  */
-/* buffered on mbarriers) when the operands meet TMA's alignment rules      */
-/* (16-byte aligned base, lda/ldb and plane strides multiples of 16 bytes)  */
-/* and otherwise runs configuration 0.  mp_gemm_tma_timeouts_P SYNCHRONIZES */
-/* and reports how many TMA waits ever ran out (always 0 unless the copy    */
-/* path failed; the kernel then returns early instead of hanging).          */
+/* Configurations 4, 5, 6 and 8 stage the tiles with TMA (cp.async.bulk.    */
+/* tensor, double buffered on mbarriers) when the operands meet TMA's       */
+/* alignment rules (16-byte aligned base, lda/ldb and plane strides         */
+/* multiples of 16 bytes) and otherwise run the same tile with plain loads. */
+/* For binary64 components configurations 5-8 use the hybrid engine: each   */
+/* TwoSum (Algorithm 2) takes s from the FP64 pipe and its error term from  */
+/* an exact integer computation (and configuration 6 likewise QuickTwoSum   */
+/* where Algorithm 1 is exact).  The bits are the FP64 sequence's; a thread */
+/* whose operands leave the integer path's domain (exponents near the       */
+/* binary64 limits, subnormal error terms, an inexact QuickTwoSum)          */
+/* recomputes its outputs with the FP64 pipe.  The built-in choice (-1) is  */
+/* configuration 5 for binary64 components, 0 for binary32.                 */
+/* mp_gemm_tma_timeouts_P SYNCHRONIZES and reports how many TMA waits ever  */
+/* ran out (always 0 unless the copy path failed; the kernel then returns   */
+/* early instead of hanging).  mp_gemm_hybrid_fallbacks_P SYNCHRONIZES and  */
+/* reports how many threads have taken the FP64 recomputation since the    */
+/* library was loaded (counted across all GEMM calls of precision P).       */
 /* ------------------------------------------------------------------------ */
 #define MPGPU_DECL_GEMM(P, T)                                                               \
     mp_status mp_gemm_##P(int opA, int opB, int64_t m, int64_t n, int64_t k, const T *A,    \
@@ -149,6 +160,7 @@ const char *mp_version(void);
                              T *C, int64_t ldc, int64_t pC, int config, mp_stream stream);  \
     int mp_gemm_num_configs_##P(void);                                                      \
     mp_status mp_gemm_tma_timeouts_##P(unsigned int *count);                                \
+    mp_status mp_gemm_hybrid_fallbacks_##P(unsigned int *count);                            \
     const char *mp_gemm_config_name_##P(int config);
 
 /* ------------------------------------------------------------------------ */

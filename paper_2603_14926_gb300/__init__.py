@@ -91,6 +91,8 @@ def _declare(L):
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
         getattr(L, f"mp_gemm_tma_timeouts_{p}").argtypes = [ctypes.POINTER(ctypes.c_uint)]
         getattr(L, f"mp_gemm_tma_timeouts_{p}").restype = _int
+        getattr(L, f"mp_gemm_hybrid_fallbacks_{p}").argtypes = [ctypes.POINTER(ctypes.c_uint)]
+        getattr(L, f"mp_gemm_hybrid_fallbacks_{p}").restype = _int
         getattr(L, f"mp_gemm_config_name_{p}").argtypes = [_int]
         getattr(L, f"mp_gemm_config_name_{p}").restype = ctypes.c_char_p
     for p in DK_PRECS:
@@ -281,6 +283,14 @@ def gemm_tma_timeouts(prec):
     """How many TMA waits of the TMA-staged GEMM ran out (synchronizes; 0 normally)."""
     v = ctypes.c_uint()
     _call(f"mp_gemm_tma_timeouts_{prec}", ctypes.byref(v))
+    return v.value
+
+
+def gemm_hybrid_fallbacks(prec):
+    """How many GEMM threads of this precision took the hybrid engine's FP64
+    recomputation since the library was loaded (synchronizes)."""
+    v = ctypes.c_uint()
+    _call(f"mp_gemm_hybrid_fallbacks_{prec}", ctypes.byref(v))
     return v.value
 
 

@@ -47,6 +47,8 @@ constexpr int64_t GEMM_GROUP = 16;  // tile rows per group of the block order
 // op(B) from global memory in the same fold order, so its bits are the FP64
 // sequence's.  Never taken on data whose components stay far from the binary64
 // range limits.
+static __device__ unsigned int mp_hybrid_fallbacks;
+
 template <class P, int TM, int TN, int NTX, int NTY>
 __device__ __noinline__ void gemm_fixup(int opA, int opB, int64_t k, const typename P::T *__restrict__ A, int64_t lda,
                                         int64_t pA, const typename P::T *__restrict__ B, int64_t ldb, int64_t pB,
@@ -56,6 +58,7 @@ __device__ __noinline__ void gemm_fixup(int opA, int opB, int64_t k, const typen
     using T = typename P::T;
     using V = typename P::V;
     NativeEngine<T> nat;
+    atomicAdd(&mp_hybrid_fallbacks, 1u);
     for (int r = 0; r < TM; r++) {
         const int64_t gi = i0 + ty + r * NTY;
         if (gi >= m) continue;
@@ -520,6 +523,11 @@ using namespace mp;
     {                                                                                              \
         if (count == nullptr) return MP_EINVAL;                                                    \
         return cuda_status(cudaMemcpyFromSymbol(count, mp_tma_timeouts, sizeof(unsigned int)));    \
+    }                                                                                              \
+    extern "C" mp_status mp_gemm_hybrid_fallbacks_##S(unsigned int *count)                         \
+    {                                                                                              \
+        if (count == nullptr) return MP_EINVAL;                                                    \
+        return cuda_status(cudaMemcpyFromSymbol(count, mp_hybrid_fallbacks, sizeof(unsigned int))); \
     }                                                                                              \
     extern "C" const char *mp_gemm_config_name_##S(int c) { return GemmTable<PT>::name(c); }
 

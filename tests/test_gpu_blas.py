@@ -129,6 +129,36 @@ def test_gemm_config0_bit_exact(mp, oracle, prec):
         assert same_bits(host(mp.gemm(prec, dev(A), dev(B), config=cfg)), want), cfg
 
 
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
+def test_gemm_hybrid_fallback_bit_exact(mp, oracle, prec):
+    """Rows of A scaled by 2^-1000 drive the error terms of their products below the
+    normal range: the hybrid engine's threads owning those rows fall back to the
+    FP64 pipe (counted), the others do not, and every configuration stays
+    bit-identical to the oracle.  A second family cancels the whole fold
+    (A = [X X], B = [Y; -Y + tiny]), which exercises QuickTwoSum outside its
+    exact case under configuration 6."""
+    K, dt = oracle.PRECS[prec]
+    m, n, k0 = 40, 36, 25
+    A = inputs.mp_uniform(11, (m, 2 * k0), K)
+    B = inputs.mp_uniform(12, (2 * k0, n), K)
+    A[:, :5, :] *= 2.0 ** -1000
+    want = oracle.gemm(prec, A, B)
+    X = inputs.mp_uniform(13, (m, k0), K)
+    Y = inputs.mp_uniform(14, (k0, n), K)
+    A2 = np.concatenate([X, X], axis=2)
+    B2 = np.concatenate([Y, -Y + inputs.mp_uniform(15, (k0, n), K) * 2.0 ** -40], axis=1)
+    want2 = oracle.gemm(prec, A2, B2)
+    for cfg in range(mp.gemm_num_configs(prec)):
+        before = mp.gemm_hybrid_fallbacks(prec)
+        assert same_bits(host(mp.gemm(prec, dev(A), dev(B), config=cfg)), want), cfg
+        taken = mp.gemm_hybrid_fallbacks(prec) - before
+        if "hybrid" in mp.gemm_config_name(prec, cfg):
+            assert 0 < taken < m * n, (cfg, taken)
+        else:
+            assert taken == 0, (cfg, taken)
+        assert same_bits(host(mp.gemm(prec, dev(A2), dev(B2), config=cfg)), want2), cfg
+
+
 @pytest.mark.parametrize("prec", ["dd", "ddc", "qd", "qf", "tf"])
 @pytest.mark.parametrize("opA,opB", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_gemm_ragged_transposed_bit_exact(mp, oracle, prec, opA, opB):
