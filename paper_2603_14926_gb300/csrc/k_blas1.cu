@@ -6,7 +6,11 @@
 // (Section 2, Algorithms 1-14).  These kernels are FP64-pipe bound for the
 // binary64 precisions (one QD multiply-add is 209 FP64 instructions against
 // 96 bytes of AXPY traffic), so each thread simply takes one element per
-// grid-stride step; loads of each plane are coalesced across the warp.
+// grid-stride step; loads of each plane are coalesced across the warp.  The
+// add, multiply, AXPY, dot and GEMV folds run on FastEngine<P> (binary64: the
+// hybrid engine, TwoSum's error term on the integer pipes); an element or a
+// thread's partial sum whose integer path left its domain is recomputed with
+// the FP64 pipe, so every result is the FP64 sequence's bits.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -56,7 +60,9 @@ __global__ void __launch_bounds__(256) k_elementwise(int64_t n, const typename P
             z = vrecip<P>(x);
         } else {
             typename P::V y = vload<P>(b, pb, i);
-            z = OP == EW_ADD ? P::add(x, y) : P::mul(x, y);
+            FastEngine<P> g;
+            z = OP == EW_ADD ? P::add(x, y, g) : P::mul(x, y, g);
+            if (g.failed()) z = OP == EW_ADD ? P::add(x, y) : P::mul(x, y);
         }
         vstore<P>(c, pc, i, z);
     }
@@ -86,7 +92,10 @@ __global__ void __launch_bounds__(256) k_axpy(int64_t n, typename P::V alpha,
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         typename P::V xi = vload<P>(x, px, i);
         typename P::V yi = vload<P>(y, py, i);
-        vstore<P>(y, py, i, P::add(P::mul(alpha, xi), yi));
+        FastEngine<P> g;
+        typename P::V r = P::add(P::mul(alpha, xi, g), yi, g);
+        if (g.failed()) r = P::add(P::mul(alpha, xi), yi);
+        vstore<P>(y, py, i, r);
     }
 }
 
@@ -173,9 +182,14 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dot_partial(int64_t n, const ty
                                                              int64_t py, typename P::T *__restrict__ part)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     typename P::V acc = vzero<P>();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        acc = P::add(acc, P::mul(vload<P>(x, px, i), vload<P>(y, py, i)));
+    FastEngine<P> g;
+    for (int64_t i = i0; i < n; i += stride) acc = P::add(acc, P::mul(vload<P>(x, px, i), vload<P>(y, py, i), g), g);
+    if (g.failed()) {  // the thread's fold again on the FP64 pipe
+        acc = vzero<P>();
+        for (int64_t i = i0; i < n; i += stride) acc = P::add(acc, P::mul(vload<P>(x, px, i), vload<P>(y, py, i)));
+    }
     acc = block_reduce<P>(acc);
     if (threadIdx.x == 0) vstore<P>(part, gridDim.x, blockIdx.x, acc);
 }
@@ -227,8 +241,14 @@ __global__ void __launch_bounds__(256) k_gemv(int64_t m, int64_t n, const typena
     typename P::V acc = vzero<P>();
     if (row < m) {
         const typename P::T *Ar = A + row * lda;
+        FastEngine<P> g;
         for (int64_t j = t; j < n; j += per_row)
-            acc = P::add(acc, P::mul(vload<P>(Ar, pA, j), vload<P>(x, px, j)));
+            acc = P::add(acc, P::mul(vload<P>(Ar, pA, j), vload<P>(x, px, j), g), g);
+        if (g.failed()) {  // the thread's fold again on the FP64 pipe
+            acc = vzero<P>();
+            for (int64_t j = t; j < n; j += per_row)
+                acc = P::add(acc, P::mul(vload<P>(Ar, pA, j), vload<P>(x, px, j)));
+        }
     }
     acc = warp_reduce<P>(acc);
     if (per_row > 32) {  // combine the row's warps (per_row / 32 of them) in shared memory

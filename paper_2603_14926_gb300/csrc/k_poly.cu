@@ -21,6 +21,13 @@
 // Polynomials from roots: one block per polynomial, the coefficient vector in
 // shared memory, one factor (x - r) or (x^2 + Bx + C) per synchronised stage,
 // all coefficients of a stage in parallel.
+//
+// Evaluation and the adjoint run on FastEngine<P> (binary64: TwoSum's error
+// term on the integer pipes).  A point whose integer path left its domain is
+// recomputed with the FP64 pipe; the coefficient wavefront, whose lanes pass
+// values to each other and to the next sweep, restarts the whole polynomial
+// on the FP64 pipe when any lane of the warp failed.  Every result is the FP64
+// sequence's bits.
 #include <cuda_runtime.h>
 
 #include "mp_arith.cuh"
@@ -31,6 +38,30 @@ namespace mp {
 // ---------------------------------------------------------------------------
 // Evaluation
 // ---------------------------------------------------------------------------
+
+template <class P, bool CPLX, class E>
+__device__ __forceinline__ void horner_point(int64_t n, const typename P::T *__restrict__ cb, int64_t pc,
+                                             const typename P::V &zr, const typename P::V &zi, typename P::V &hr,
+                                             typename P::V &hi, E &g)
+{
+    using V = typename P::V;
+    hr = vload<P>(cb, pc, n);
+    hi = vzero<P>();
+    if (!CPLX) {
+        for (int64_t i = n - 1; i >= 0; i--) hr = P::add(P::mul(hr, zr, g), vload<P>(cb, pc, i), g);
+    } else {
+        for (int64_t i = n - 1; i >= 0; i--) {
+            V t1 = P::mul(hr, zr, g);
+            V t2 = P::mul(hi, zi, g);
+            t1 = vsub<P>(t1, t2, g);
+            t1 = P::add(t1, vload<P>(cb, pc, i), g);
+            V t3 = P::mul(hr, zi, g);
+            V t4 = P::mul(hi, zr, g);
+            hi = P::add(t3, t4, g);
+            hr = t1;
+        }
+    }
+}
 
 template <class P, bool CPLX>
 __global__ void __launch_bounds__(256) k_polyeval(int64_t npoly, const int64_t *__restrict__ coef_off,
@@ -54,26 +85,16 @@ __global__ void __launch_bounds__(256) k_polyeval(int64_t npoly, const int64_t *
             continue;
         }
         const V zr = vload<P>(xr, px, idx);
-        V hr = vload<P>(cb, pc, n);
-        if (!CPLX) {
-            for (int64_t i = n - 1; i >= 0; i--) hr = P::add(P::mul(hr, zr), vload<P>(cb, pc, i));
-            vstore<P>(yr, py, idx, hr);
-        } else {
-            const V zi = vload<P>(xi, px, idx);
-            V hi = vzero<P>();
-            for (int64_t i = n - 1; i >= 0; i--) {
-                V t1 = P::mul(hr, zr);
-                V t2 = P::mul(hi, zi);
-                t1 = vsub<P>(t1, t2);
-                t1 = P::add(t1, vload<P>(cb, pc, i));
-                V t3 = P::mul(hr, zi);
-                V t4 = P::mul(hi, zr);
-                hi = P::add(t3, t4);
-                hr = t1;
-            }
-            vstore<P>(yr, py, idx, hr);
-            vstore<P>(yi, py, idx, hi);
+        const V zi = CPLX ? vload<P>(xi, px, idx) : vzero<P>();
+        V hr, hi;
+        FastEngine<P> g;
+        horner_point<P, CPLX>(n, cb, pc, zr, zi, hr, hi, g);
+        if (g.failed()) {
+            NativeEngine<typename P::T> nat;
+            horner_point<P, CPLX>(n, cb, pc, zr, zi, hr, hi, nat);
         }
+        vstore<P>(yr, py, idx, hr);
+        if (CPLX) vstore<P>(yi, py, idx, hi);
     }
 }
 
@@ -104,6 +125,21 @@ static mp_status polyeval_launch(int64_t npoly, const int64_t *coef_off, const t
 // Adjoint
 // ---------------------------------------------------------------------------
 
+// dy_m p'(x_m) by the simultaneous Horner recurrence for p and p'.
+template <class P, class E>
+__device__ __forceinline__ typename P::V dx_point(int64_t n, const typename P::T *__restrict__ cb, int64_t pc,
+                                                  const typename P::V &xm, const typename P::V &dym, E &g)
+{
+    using V = typename P::V;
+    V h = vload<P>(cb, pc, n);
+    V d = vzero<P>();
+    for (int64_t i = n - 1; i >= 0; i--) {
+        d = P::add(P::mul(d, xm, g), h, g);
+        h = P::add(P::mul(h, xm, g), vload<P>(cb, pc, i), g);
+    }
+    return P::mul(dym, d, g);
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *__restrict__ coef_off,
                                                  const typename P::T *__restrict__ coef, int64_t pc,
@@ -124,17 +160,55 @@ __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *_
         }
         const typename P::T *cb = coef + off;
         const V xm = vload<P>(x, px, idx);
-        V h = vload<P>(cb, pc, n);
-        V d = vzero<P>();
-        for (int64_t i = n - 1; i >= 0; i--) {
-            d = P::add(P::mul(d, xm), h);
-            h = P::add(P::mul(h, xm), vload<P>(cb, pc, i));
+        const V dym = vload<P>(dy, pdy, idx);
+        FastEngine<P> g;
+        V r = dx_point<P>(n, cb, pc, xm, dym, g);
+        if (g.failed()) {
+            NativeEngine<typename P::T> nat;
+            r = dx_point<P>(n, cb, pc, xm, dym, nat);
         }
-        vstore<P>(dx, pdx, idx, P::mul(vload<P>(dy, pdy, idx), d));
+        vstore<P>(dx, pdx, idx, r);
     }
 }
 
 constexpr int DCOEF_WARPS = 4;
+
+// All coefficient sweeps of one polynomial (one warp).  Returns true, after the
+// sweep in which it happened, when any lane's engine failed; the caller then
+// starts again from the first sweep (dy is never overwritten) on the FP64 pipe.
+template <class P, class E>
+__device__ __forceinline__ bool dcoef_sweeps(int64_t n, int64_t off, int64_t base, int64_t npts,
+                                             const typename P::T *__restrict__ x, int64_t px,
+                                             const typename P::T *__restrict__ dy, int64_t pdy,
+                                             typename P::T *__restrict__ dcoef, int64_t pdc,
+                                             typename P::T *__restrict__ wbuf, int64_t pw, E &g)
+{
+    using V = typename P::V;
+    const int lane = threadIdx.x & 31;
+    for (int64_t j0 = 0; j0 <= n; j0 += 32) {
+        const int64_t i = j0 + lane;
+        V S = vzero<P>();
+        V win = vzero<P>();
+        for (int64_t s = 0; s < npts + 31; s++) {
+            const int64_t m = s - lane;
+            const bool act = m >= 0 && m < npts && i <= n;
+            V w = win;
+            if (lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
+            V wout = vzero<P>();
+            if (act) {
+                S = P::add(S, w, g);
+                if (i < n) wout = P::mul(w, vload<P>(x, px, base + m), g);
+            }
+            if (lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout);
+#pragma unroll
+            for (int c = 0; c < P::K; c++) win.c[c] = __shfl_up_sync(0xffffffffu, wout.c[c], 1);
+        }
+        if (__any_sync(0xffffffffu, g.failed())) return true;
+        if (i <= n) vstore<P>(dcoef, pdc, off + i, S);
+        __syncwarp();
+    }
+    return false;
+}
 
 template <class P>
 __global__ void __launch_bounds__(32 * DCOEF_WARPS)
@@ -151,26 +225,10 @@ __global__ void __launch_bounds__(32 * DCOEF_WARPS)
     const int64_t n = coef_off[b + 1] - off - 1;
     if (n < 0) return;
     const int64_t base = b * npts;  // this polynomial's points
-    for (int64_t j0 = 0; j0 <= n; j0 += 32) {
-        const int64_t i = j0 + lane;
-        V S = vzero<P>();
-        V win = vzero<P>();
-        for (int64_t s = 0; s < npts + 31; s++) {
-            const int64_t m = s - lane;
-            const bool act = m >= 0 && m < npts && i <= n;
-            V w = win;
-            if (lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
-            V wout = vzero<P>();
-            if (act) {
-                S = P::add(S, w);
-                if (i < n) wout = P::mul(w, vload<P>(x, px, base + m));
-            }
-            if (lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout);
-#pragma unroll
-            for (int c = 0; c < P::K; c++) win.c[c] = __shfl_up_sync(0xffffffffu, wout.c[c], 1);
-        }
-        if (i <= n) vstore<P>(dcoef, pdc, off + i, S);
-        __syncwarp();
+    FastEngine<P> g;
+    if (dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, g)) {
+        NativeEngine<typename P::T> nat;
+        dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, nat);
     }
 }
 

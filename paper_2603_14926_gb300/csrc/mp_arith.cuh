@@ -15,6 +15,7 @@
 // needs.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "mp_eft_int.cuh"
 
@@ -362,6 +363,13 @@ MP_PREC_TAG(P_tf, float, 3, tw_add_bf<float>, tw_mul_bf<float>, 2, false)
 MP_PREC_TAG(P_qf, float, 4, qw_add_bf<float>, qw_mul_bf<float>, 3, false)
 #undef MP_PREC_TAG
 
+// The engine the library's kernels use by default: hybrid for binary64
+// components (every result still the FP64 sequence's bits, see above), native
+// for binary32 components (their FP32 pipe is 64x wider, no gain).
+template <class P>
+using FastEngine =
+    typename std::conditional<P::fp64, HybridEngine<false>, NativeEngine<typename P::T>>::type;
+
 // ---------------------------------------------------------------------------
 // Helpers over K-component values
 // ---------------------------------------------------------------------------
@@ -394,6 +402,12 @@ template <class P>
 __device__ __forceinline__ typename P::V vsub(const typename P::V &a, const typename P::V &b)
 {
     return P::add(a, vneg<P>(b));
+}
+
+template <class P, class E>
+__device__ __forceinline__ typename P::V vsub(const typename P::V &a, const typename P::V &b, E &g)
+{
+    return P::add(a, vneg<P>(b), g);
 }
 
 // Load / store element i of a K-array in plane layout (component c at base[c*ps + i]).

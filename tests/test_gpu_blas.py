@@ -48,7 +48,7 @@ def pbits(prec):
 @pytest.mark.parametrize("prec", ALL)
 def test_elementwise_bit_exact(mp, oracle, prec):
     K, dt = oracle.PRECS[prec]
-    for name, a, b in families(oracle, prec, n=1537, seed=3):
+    for name, a, b in families(oracle, prec, n=1537, seed=3, limits=True):
         da, db = dev(a), dev(b)
         assert same_bits(host(mp.add(prec, da, db)), oracle.add(prec, a, b)), name
         assert same_bits(host(mp.mul(prec, da, db)), oracle.mul(prec, a, b)), name
@@ -66,6 +66,12 @@ def test_axpy_bit_exact(mp, oracle, prec):
     dy = dev(y)
     mp.axpy(prec, alpha, dev(x), dy)
     assert same_bits(host(dy), oracle.axpy(prec, alpha, x, y))
+    if dt == np.float64:  # operands near the ends of the range: the FP64 recomputation path
+        x[:, 0::5] *= 2.0 ** -1000
+        y[:, 1::5] *= 2.0 ** 1000
+        dy = dev(y)
+        mp.axpy(prec, alpha, dev(x), dy)
+        assert same_bits(host(dy), oracle.axpy(prec, alpha, x, y))
 
 
 @pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd", "qf"])
@@ -96,6 +102,29 @@ def test_dot_workspace_errors(mp):
     small = torch.empty(8, dtype=torch.uint8, device="cuda")
     with pytest.raises(mp.MPError, match="workspace"):
         mp.dot("qd", x, x, ws=small)
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_dot_gemv_range_limits_match_fp64_fold(mp, oracle, prec):
+    """Every fourth column of A (and element of x for the dot) scaled by 2^-1000:
+    the threads whose partial folds meet them recompute on the FP64 pipe.  The
+    one-column GEMM (sequential fold) matches the oracle bit for bit; GEMV and
+    dot, which reduce in a tree, agree with the sequential folds to 1e-12
+    relative (no error bound of the paper applies in the subnormal range, so this
+    checks that the recomputed partials are the right ones, not garbage)."""
+    K, dt = oracle.PRECS[prec]
+    n = 700
+    A = inputs.mp_uniform(21, (3, n), K)
+    x = inputs.mp_uniform(22, n, K, stream=inputs.STREAM_X)
+    A[:, :, 0::4] *= 2.0 ** -1000
+    want = oracle.gemm(prec, A, x.reshape(K, n, 1))[:, :, 0]
+    g = host(mp.gemm(prec, dev(A), dev(x.reshape(K, n, 1))))[:, :, 0]
+    assert same_bits(g, want)
+    y = host(mp.gemv(prec, dev(A), dev(x)))
+    for i in range(3):
+        assert abs(float(y[0, i]) - float(want[0, i])) <= 1e-12 * max(1.0, abs(float(want[0, i])))
+    d = host(mp.dot(prec, dev(np.ascontiguousarray(A[:, 0, :])), dev(x)))
+    assert abs(float(d[0]) - float(want[0, 0])) <= 1e-12 * max(1.0, abs(float(want[0, 0])))
 
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "tf"])

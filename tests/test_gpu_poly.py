@@ -56,6 +56,26 @@ def test_polyeval_backward_bit_exact(mp, oracle, prec, npts):
     assert same_bits(host(dx), wx)
 
 
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_horner_range_limits_bit_exact(mp, oracle, prec):
+    """Points and adjoint seeds near the bottom of the binary64 range send the
+    hybrid engine to its FP64 recomputation (per point for values and dx, per
+    polynomial for the coefficient wavefront); every result stays bit-identical
+    to the oracle."""
+    K, dt = oracle.PRECS[prec]
+    off, coef = ragged(8, 6, 0, 70, K, dt)
+    npoly, npts = len(off) - 1, 40
+    x = inputs.mp_uniform(9, npoly * npts, K, dt, stream=inputs.STREAM_X)
+    dy = inputs.mp_uniform(10, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    x[:, 0::7] *= 2.0 ** -1000
+    dy[:, 2 * npts:3 * npts] *= 2.0 ** -1000
+    doff, dcoef = dev(off), dev(coef)
+    assert same_bits(host(mp.polyeval(prec, doff, dcoef, npts, dev(x))), oracle.polyeval(prec, off, coef, npts, x))
+    dc, dx = mp.polyeval_backward(prec, doff, dcoef, npts, dev(x), dev(dy))
+    wc, wx = oracle.polyeval_backward(prec, off, coef, npts, x, dy)
+    assert same_bits(host(dc), wc) and same_bits(host(dx), wx)
+
+
 def test_polyeval_backward_workspace_checked(mp, oracle):
     import torch
 
