@@ -41,11 +41,20 @@ import numpy as np  # noqa: E402
 INSTR_MUL = {"dd": 9, "ddc": 9, "td": 39, "qd": 106, "ds": 9, "tf": 39, "qf": 106}
 INSTR_ADD = {"dd": 20, "ddc": 11, "td": 57, "qd": 103, "ds": 20, "tf": 57, "qf": 103}
 FMA_PER_MUL = {"dd": 1, "ddc": 1, "td": 3, "qd": 6, "ds": 1, "tf": 3, "qf": 6}
-# TwoSum (Algorithm 2) calls per multiply-add: add + multiply.  The hybrid engine
-# issues one FP64 add for each instead of six and takes the error term from the
-# integer pipes, so a hybrid multiply-add issues mac_instr - 5 * TWO_SUMS FP64
-# instructions.
-TWO_SUMS = {"dd": 2, "ddc": 1, "td": 9, "qd": 22}
+# TwoSum (Algorithm 2) calls per add and per multiply.  The hybrid engine issues
+# one FP64 add for each instead of six and takes the error term from the integer
+# pipes, so a hybrid add issues INSTR_ADD - 5 * TWO_SUMS_ADD FP64 instructions.
+TWO_SUMS_ADD = {"dd": 2, "ddc": 1, "td": 7, "qd": 11}
+TWO_SUMS_MUL = {"dd": 0, "ddc": 0, "td": 2, "qd": 11}
+TWO_SUMS = {p: TWO_SUMS_ADD[p] + TWO_SUMS_MUL[p] for p in TWO_SUMS_ADD}
+
+
+def add_instr(prec, hybrid=True):
+    return INSTR_ADD[prec] - (5 * TWO_SUMS_ADD.get(prec, 0) if hybrid else 0)
+
+
+def mul_instr(prec, hybrid=True):
+    return INSTR_MUL[prec] - (5 * TWO_SUMS_MUL.get(prec, 0) if hybrid else 0)
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 dense FP64, FMA = 2 flops
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SM_MAX_MHZ = 2070.0
@@ -57,7 +66,7 @@ def mac_instr(prec):
 
 def mac_instr_hybrid(prec):
     """FP64-pipe instructions of one multiply-add under the hybrid engine."""
-    return mac_instr(prec) - 5 * TWO_SUMS.get(prec, 0)
+    return add_instr(prec) + mul_instr(prec)
 
 
 # ---------------------------------------------------------------------------
@@ -300,8 +309,13 @@ def extras(prec="qd", quick=False):
 
     out = {}
     K = mpg.PRECS[prec][0]
-    ins = mac_instr(prec)
+    # FP64 instructions these kernels issue (hybrid engine for binary64) and the
+    # paper's all-FP64 sequence they reproduce bit for bit
+    ins, ins_paper = mac_instr_hybrid(prec), mac_instr(prec)
     peak = NOMINAL_FP64_TFLOPS * 1e12 / 2
+
+    def rates(fp64, paper, t):
+        return {"fp64_instr_frac": fp64 / t / peak, "paper_sequence_equiv_frac": paper / t / peak}
 
     def timed(fn, reps=3):
         fn()
@@ -319,19 +333,18 @@ def extras(prec="qd", quick=False):
     x = dev(inputs.mp_uniform(1, n, K, stream=inputs.STREAM_X))
     y = dev(inputs.mp_uniform(1, n, K, stream=inputs.STREAM_Y))
     t = timed(lambda: mpg.axpy(prec, [0.5] + [0.0] * (K - 1), x, y))
-    out["axpy"] = {"n": n, "ms": t * 1e3, "GB/s": 3 * K * 8 * n / t / 1e9,
-                   "fp64_instr_frac": n * ins / t / peak}
+    out["axpy"] = {"n": n, "ms": t * 1e3, "GB/s": 3 * K * 8 * n / t / 1e9, **rates(n * ins, n * ins_paper, t)}
     ws = torch.empty(mpg.dot_workspace(prec, n), dtype=torch.uint8, device="cuda")
     r = mpg.empty(prec)
     t = timed(lambda: mpg.dot(prec, x, y, out=r, ws=ws))
-    out["dot"] = {"n": n, "ms": t * 1e3, "fp64_instr_frac": n * ins / t / peak}
+    out["dot"] = {"n": n, "ms": t * 1e3, **rates(n * ins, n * ins_paper, t)}
     del x, y
     m = 8192
     A = dev(inputs.mp_uniform(2, (m, m), K))
     xv = dev(inputs.mp_uniform(3, m, K, stream=inputs.STREAM_X))
     yv = mpg.empty(prec, m)
     t = timed(lambda: mpg.gemv(prec, A, xv, out=yv))
-    out["gemv"] = {"m": m, "n": m, "ms": t * 1e3, "fp64_instr_frac": m * m * ins / t / peak}
+    out["gemv"] = {"m": m, "n": m, "ms": t * 1e3, **rates(m * m * ins, m * m * ins_paper, t)}
     del A
     # complex GEMM by the 3M method (Eq. 3) vs the real GEMM, n = 1024, Eq. 2 entries
     nc = 512 if quick else 1024
@@ -344,7 +357,7 @@ def extras(prec="qd", quick=False):
     tr = timed(lambda: mpg.gemm(prec, Ar, Br, out=Cr), reps=1)
     out["complex_gemm_3m"] = {"n": nc, "ms": tc * 1e3, "real_gemm_ms": tr * 1e3, "complex_over_real": tc / tr,
                               "complex_qd_ops_per_s": 8.0 * nc ** 3 / tc,
-                              "fp64_instr_frac": 3 * nc ** 3 * ins / tc / peak}
+                              **rates(3 * nc ** 3 * ins, 3 * nc ** 3 * ins_paper, tc)}
     del Ar, Ai, Br, Bi, Cr, Ci
     # Horner forward/backward: 1024 polynomials, degree 256, 4096 real points each
     npoly, deg, npts = (256 if quick else 1024), 256, 4096
@@ -355,12 +368,13 @@ def extras(prec="qd", quick=False):
     t = timed(lambda: mpg.polyeval(prec, off, coef, npts, xs), reps=1)
     steps = npoly * npts * deg
     out["horner_fwd"] = {"polys": npoly, "degree": deg, "points": npts, "ms": t * 1e3,
-                         "fp64_instr_frac": steps * ins / t / peak}
+                         **rates(steps * ins, steps * ins_paper, t)}
     wsb = torch.empty(mpg.polyeval_backward_workspace(prec, npoly, npts), dtype=torch.uint8, device="cuda")
     tb = timed(lambda: mpg.polyeval_backward(prec, off, coef, npts, xs, dy, ws=wsb), reps=1)
     # dx: 2 mul + 2 add per step (+1 mul), dcoef: 1 mul + 1 add per (coefficient, point)
-    bw_instr = steps * 2 * ins + npoly * npts * INSTR_MUL[prec] + npoly * npts * (deg + 1) * ins
-    out["horner_bwd"] = {"ms": tb * 1e3, "vs_fwd": tb / t, "fp64_instr_frac": bw_instr / tb / peak}
+    bw = lambda i, mu: steps * 2 * i + npoly * npts * mu + npoly * npts * (deg + 1) * i  # noqa: E731
+    out["horner_bwd"] = {"ms": tb * 1e3, "vs_fwd": tb / t,
+                         **rates(bw(ins, mul_instr(prec)), bw(ins_paper, INSTR_MUL[prec]), tb)}
     return out
 
 
