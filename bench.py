@@ -592,7 +592,8 @@ def profile_one(a):
             mpg.polyeval_backward(prec, off, coef, npts, xs, xs, want_dx=False)
     elif a.profile == "peak":
         names = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "FFMA", 4: "FADD", 5: "FFMA2 (f32x2, per lane)",
-                 6: "FADD2 (f32x2, per lane)"}
+                 6: "FADD2 (f32x2, per lane)", 7: "LOP3 (integer ALU pipe)", 8: "IMAD (integer, FMA pipe)",
+                 9: "IADD3 | LOP3 alternating", 10: "FLO + IADD3 (2 per op)"}
         res = {}
         sms = mpg.lib().mp_sm_count()
         for kind, nm in names.items():
@@ -603,7 +604,8 @@ def profile_one(a):
                 rate, _ = mpg.peak(kind, iters=it, blocks=sms * per_sm, threads=thr)
                 best = max(best, rate)
             res[nm] = best / 1e9
-        print(json.dumps({"lane_instr_per_s_G": res, "sms": sms}))
+        per_sm_clk = {k: v * 1e9 / sms / (SM_MAX_MHZ * 1e6) for k, v in res.items()}
+        print(json.dumps({"lane_instr_per_s_G": res, "lanes_per_clk_per_sm_at_max_clock": per_sm_clk, "sms": sms}))
         return
     elif a.profile == "dk":
         prob = inputs.dk_problem(3, a.n, 10, 500)

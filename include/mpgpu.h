@@ -271,7 +271,9 @@ mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off
 /* a clock64 budget per polynomial) stopped it.  Results, iteration counts  */
 /* and statuses are bit-identical to the CPU oracle and identical between   */
 /* the persistent batched launch (mode 0) and one launch per polynomial     */
-/* (mode 1).                                                                */
+/* (mode 1).  The per-root update runs on the hybrid engine (TwoSum error  */
+/* terms on the integer pipes, see GEMM) and is recomputed on the FP64 pipe */
+/* for any root whose integer path leaves its domain: same bits.            */
 /*   roots  : complex K-array, root j of polynomial b at index              */
 /*            coef_off[b] - b + j, plane stride proots                       */
 /*   z0     : NULL or starting values in the same layout (plane stride pz0)  */
@@ -290,7 +292,7 @@ typedef struct {
     double radius;           /* > 0: start circle radius instead of Eq. 5's */
     int64_t watchdog_cycles; /* > 0: per-polynomial clock64 budget, status 3 when spent */
     int32_t max_degree;      /* host bound on every degree, required */
-    int32_t threads;         /* threads per block, 0 = automatic (multiple of 32) */
+    int32_t threads;         /* threads per block: 0 = 256; else a multiple of 32, <= 256 */
     int32_t blocks_per_sm;   /* persistent grid = SMs * blocks_per_sm, 0 = automatic */
     int32_t sort;            /* 1: process polynomials in descending degree (default 0 = off) */
 } mp_roots_opts;
@@ -339,10 +341,12 @@ MPGPU_DECL_ROOTS(qd)
 /* Pipe-peak microbenchmark (measurement support, not part of the method):   */
 /* `blocks` x `threads` threads each run `iters` iterations of 8 independent */
 /* dependency chains of one instruction kind: 0 = DFMA, 1 = DADD, 2 = DMUL,  */
-/* 3 = FFMA, 4 = FADD, 5 = packed fma.rn.f32x2, 6 = packed add.rn.f32x2.     */
+/* 3 = FFMA, 4 = FADD, 5 = packed fma.rn.f32x2, 6 = packed add.rn.f32x2,     */
+/* 7 = LOP3 (integer ALU pipe), 8 = IMAD (integer on the FMA pipe),          */
+/* 9 = IADD3 and LOP3 alternating, 10 = FLO + IADD3 (count leading zeros).   */
 /* SYNCHRONIZES the stream; *ms receives the elapsed time between CUDA      */
 /* events recorded on it and *lane_ops the number of per-lane operations     */
-/* executed (blocks * threads * iters * 8, doubled for the packed kinds).   */
+/* executed (blocks * threads * iters * 8, doubled for kinds 5, 6 and 10).  */
 /* ------------------------------------------------------------------------ */
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms,
                       double *lane_ops, mp_stream stream);

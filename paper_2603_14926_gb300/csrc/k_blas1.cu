@@ -317,7 +317,28 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
 template <int KIND>
 __global__ void k_peak(int64_t iters, double *sink)
 {
-    if (KIND >= 5) {
+    if (KIND >= 7) {  // integer pipes; inline PTX so the chains cannot be folded
+        unsigned a[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = threadIdx.x * 7u + (unsigned)j;
+        const unsigned b = 0x12345u, cc = 0x9abcu;
+        for (int64_t it = 0; it < iters; it++) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (KIND == 7) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[j]) : "r"(b), "r"(cc));
+                if (KIND == 8) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[j]) : "r"(b), "r"(cc));
+                if (KIND == 9) {
+                    if (j & 1) asm volatile("add.u32 %0, %0, %1;" : "+r"(a[j]) : "r"(b));
+                    else asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[j]) : "r"(b), "r"(cc));
+                }
+                if (KIND == 10) asm volatile("{.reg .u32 t; clz.b32 t, %0; add.u32 %0, %0, t;}" : "+r"(a[j]));
+            }
+        }
+        unsigned s = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) s ^= a[j];
+        if (s == 0x7777777u) sink[0] = (double)s;
+    } else if (KIND >= 5) {
         unsigned long long a[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) a[j] = 0x3f8000003f800000ULL + threadIdx.x + j;  // ~(1.0f, 1.0f)
@@ -394,7 +415,7 @@ int mp_sm_count(void) { return sm_count(); }
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms, double *lane_ops,
                       mp_stream stream)
 {
-    if (kind < 0 || kind > 6 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
+    if (kind < 0 || kind > 10 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
         ms == nullptr || lane_ops == nullptr)
         return MP_EINVAL;
     cudaStream_t s = as_stream(stream);
@@ -414,13 +435,17 @@ mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *m
     case 3: k_peak<3><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 4: k_peak<4><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 5: k_peak<5><<<blocks, threads, 0, s>>>(iters, nullptr); break;
-    default: k_peak<6><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 6: k_peak<6><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 7: k_peak<7><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 8: k_peak<8><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 9: k_peak<9><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    default: k_peak<10><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     }
     st = launch_status();
     cudaEventRecord(e1, s);
     if (st == MP_OK) st = cuda_status(cudaEventSynchronize(e1));
     if (st == MP_OK) st = cuda_status(cudaEventElapsedTime(ms, e0, e1));
-    *lane_ops = (double)blocks * threads * (double)iters * 8.0 * (kind >= 5 ? 2.0 : 1.0);
+    *lane_ops = (double)blocks * threads * (double)iters * 8.0 * ((kind == 5 || kind == 6 || kind == 10) ? 2.0 : 1.0);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;

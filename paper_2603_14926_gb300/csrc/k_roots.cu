@@ -219,6 +219,77 @@ __device__ void block_max2(DKShared &sh, double a, double b, int bad)
     __syncthreads();
 }
 
+// One root's Durand-Kerner update (Eq. 4): w_i = q(z_i) / prod_{j != i} (z_i - z_j)
+// with extended exponents for both factors, y_i = z_i - w_i; every multicomponent
+// operation on the engine g.
+template <class P, class E>
+__device__ __forceinline__ void dk_update(int64_t i, int64_t n, const double *c, int64_t cap, const double *z,
+                                          int64_t zc, const typename P::V &zr, const typename P::V &zi,
+                                          typename P::V &yr, typename P::V &yi, typename P::V &wr,
+                                          typename P::V &wi, E &g)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    // q(z_i) with extended exponent
+    V hr = vload<P>(c, cap, n), hi = vzero<P>();
+    long long Eq = 0;
+    for (int64_t kk = n - 1; kk >= 0; kk--) {
+        V a = vload<P>(c, cap, kk);
+        if (Eq > 1000) a = vzero<P>();
+        else if (Eq > 0) vscale<P>(a, (int)-Eq);
+        V t1 = P::mul(hr, zr, g);
+        V t2 = P::mul(hi, zi, g);
+        t1 = vsub<P>(t1, t2, g);
+        t1 = P::add(t1, a, g);
+        V t3 = P::mul(hr, zi, g);
+        V t4 = P::mul(hi, zr, g);
+        hi = P::add(t3, t4, g);
+        hr = t1;
+        const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+        if (be >= 1023 + DK_RESCALE + 1) {
+            vscale<P>(hr, -DK_RESCALE);
+            vscale<P>(hi, -DK_RESCALE);
+            Eq += DK_RESCALE;
+        }
+    }
+    // prod_{j != i} (z_i - z_j) with extended exponent
+    V dr = vone<P>(), di = vzero<P>();
+    long long Ed = 0;
+    for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        const V tr = vsub<P>(zr, vload<P>(z, zc, j), g);
+        const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, j), g);
+        cmul<P>(dr, di, tr, ti, dr, di, g);
+        const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
+        if (be >= 1023 + DK_RESCALE + 1) {
+            vscale<P>(dr, -DK_RESCALE);
+            vscale<P>(di, -DK_RESCALE);
+            Ed += DK_RESCALE;
+        } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
+            vscale<P>(dr, DK_RESCALE);
+            vscale<P>(di, DK_RESCALE);
+            Ed -= DK_RESCALE;
+        }
+    }
+    cdiv<P>(hr, hi, dr, di, wr, wi, g);
+    vscale_big<P>(wr, Eq - Ed);
+    vscale_big<P>(wi, Eq - Ed);
+    yr = vsub<P>(zr, wr, g);
+    yi = vsub<P>(zi, wi, g);
+}
+
+// The same update on the FP64 pipe, out of line: taken only when the hybrid
+// engine left its domain, so it need not share the hot path's registers.
+template <class P>
+__device__ __noinline__ void dk_update_native(int64_t i, int64_t n, const double *c, int64_t cap, const double *z,
+                                              int64_t zc, const typename P::V &zr, const typename P::V &zi,
+                                              typename P::V &yr, typename P::V &yi, typename P::V &wr,
+                                              typename P::V &wi)
+{
+    NativeEngine<double> nat;
+    dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, nat);
+}
+
 template <class P>
 __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *smem)
 {
@@ -311,52 +382,10 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
         int bad = 0;
         for (int64_t i = tid; i < n; i += nt) {
             const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
-            // q(z_i) with extended exponent
-            V hr = vload<P>(c, cap, n), hi = vzero<P>();
-            long long Eq = 0;
-            for (int64_t kk = n - 1; kk >= 0; kk--) {
-                V a = vload<P>(c, cap, kk);
-                if (Eq > 1000) a = vzero<P>();
-                else if (Eq > 0) vscale<P>(a, (int)-Eq);
-                V t1 = P::mul(hr, zr);
-                V t2 = P::mul(hi, zi);
-                t1 = vsub<P>(t1, t2);
-                t1 = P::add(t1, a);
-                V t3 = P::mul(hr, zi);
-                V t4 = P::mul(hi, zr);
-                hi = P::add(t3, t4);
-                hr = t1;
-                const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
-                if (be >= 1023 + DK_RESCALE + 1) {
-                    vscale<P>(hr, -DK_RESCALE);
-                    vscale<P>(hi, -DK_RESCALE);
-                    Eq += DK_RESCALE;
-                }
-            }
-            // prod_{j != i} (z_i - z_j) with extended exponent
-            V dr = vone<P>(), di = vzero<P>();
-            long long Ed = 0;
-            for (int64_t j = 0; j < n; j++) {
-                if (j == i) continue;
-                const V tr = vsub<P>(zr, vload<P>(z, zc, j));
-                const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, j));
-                cmul<P>(dr, di, tr, ti, dr, di);
-                const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
-                if (be >= 1023 + DK_RESCALE + 1) {
-                    vscale<P>(dr, -DK_RESCALE);
-                    vscale<P>(di, -DK_RESCALE);
-                    Ed += DK_RESCALE;
-                } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
-                    vscale<P>(dr, DK_RESCALE);
-                    vscale<P>(di, DK_RESCALE);
-                    Ed -= DK_RESCALE;
-                }
-            }
-            V wr, wi;
-            cdiv<P>(hr, hi, dr, di, wr, wi);
-            vscale_big<P>(wr, Eq - Ed);
-            vscale_big<P>(wi, Eq - Ed);
-            const V yr = vsub<P>(zr, wr), yi = vsub<P>(zi, wi);
+            V yr, yi, wr, wi;
+            FastEngine<P> g;
+            dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
+            if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
             vstore<P>(zn, pn, i, yr);
             vstore<P>(zn + K * pn, pn, i, yi);
             const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
@@ -397,7 +426,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
 }
 
 template <class P>
-__global__ void __launch_bounds__(256) k_dk_persistent(DKArgs<P> A)
+__global__ void __launch_bounds__(256, 2) k_dk_persistent(DKArgs<P> A)
 {
     extern __shared__ __align__(16) double dk_smem[];
     __shared__ DKShared sh;
@@ -413,7 +442,7 @@ __global__ void __launch_bounds__(256) k_dk_persistent(DKArgs<P> A)
 }
 
 template <class P>
-__global__ void __launch_bounds__(256) k_dk_single(DKArgs<P> A, int64_t p)
+__global__ void __launch_bounds__(256, 2) k_dk_single(DKArgs<P> A, int64_t p)
 {
     extern __shared__ __align__(16) double dk_smem[];
     __shared__ DKShared sh;
@@ -498,7 +527,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         return MP_EINVAL;
     if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
     if (o->mode != 0 && o->mode != 1) return MP_EINVAL;
-    const int threads = o->threads > 0 ? o->threads : 128;
+    const int threads = o->threads > 0 ? o->threads : 256;
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
     if (ws == nullptr) return MP_EINVAL;

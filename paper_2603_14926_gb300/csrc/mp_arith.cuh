@@ -431,7 +431,7 @@ __device__ __forceinline__ void vstore(typename P::T *__restrict__ base, int64_t
 
 // Reciprocal by Newton's method (Section 2 leaves the scheme open): y0 = 1/x[0]
 // (one correctly rounded division), then newton_steps times e = 1 - x*y, y = y + y*e.
-template <class P> __device__ __forceinline__ typename P::V vrecip(const typename P::V &x)
+template <class P, class E> __device__ __forceinline__ typename P::V vrecip(const typename P::V &x, E &g)
 {
     using T = typename P::T;
     typename P::V y = vzero<P>();
@@ -439,39 +439,59 @@ template <class P> __device__ __forceinline__ typename P::V vrecip(const typenam
     const typename P::V one = vone<P>();
 #pragma unroll 1
     for (int s = 0; s < P::newton_steps; s++) {
-        typename P::V t = P::mul(x, y);
-        typename P::V e = vsub<P>(one, t);
-        y = P::add(y, P::mul(y, e));
+        typename P::V t = P::mul(x, y, g);
+        typename P::V e = vsub<P>(one, t, g);
+        y = P::add(y, P::mul(y, e, g), g);
     }
     return y;
 }
 
-// Complex product with four real products: re = ar*br - ai*bi, im = ar*bi + ai*br.
-template <class P>
-__device__ __forceinline__ void cmul(const typename P::V &ar, const typename P::V &ai,
-                                     const typename P::V &br, const typename P::V &bi,
-                                     typename P::V &cr, typename P::V &ci)
+template <class P> __device__ __forceinline__ typename P::V vrecip(const typename P::V &x)
 {
-    typename P::V t1 = P::mul(ar, br);
-    typename P::V t2 = P::mul(ai, bi);
-    typename P::V t3 = P::mul(ar, bi);
-    typename P::V t4 = P::mul(ai, br);
-    cr = vsub<P>(t1, t2);
-    ci = P::add(t3, t4);
+    NativeEngine<typename P::T> g;
+    return vrecip<P>(x, g);
+}
+
+// Complex product with four real products: re = ar*br - ai*bi, im = ar*bi + ai*br.
+template <class P, class E>
+__device__ __forceinline__ void cmul(const typename P::V &ar, const typename P::V &ai, const typename P::V &br,
+                                     const typename P::V &bi, typename P::V &cr, typename P::V &ci, E &g)
+{
+    typename P::V t1 = P::mul(ar, br, g);
+    typename P::V t2 = P::mul(ai, bi, g);
+    typename P::V t3 = P::mul(ar, bi, g);
+    typename P::V t4 = P::mul(ai, br, g);
+    cr = vsub<P>(t1, t2, g);
+    ci = P::add(t3, t4, g);
+}
+
+template <class P>
+__device__ __forceinline__ void cmul(const typename P::V &ar, const typename P::V &ai, const typename P::V &br,
+                                     const typename P::V &bi, typename P::V &cr, typename P::V &ci)
+{
+    NativeEngine<typename P::T> g;
+    cmul<P>(ar, ai, br, bi, cr, ci, g);
 }
 
 // Complex quotient a / b = (a * conj b) * recip(br^2 + bi^2).
-template <class P>
-__device__ __forceinline__ void cdiv(const typename P::V &ar, const typename P::V &ai,
-                                     const typename P::V &br, const typename P::V &bi,
-                                     typename P::V &cr, typename P::V &ci)
+template <class P, class E>
+__device__ __forceinline__ void cdiv(const typename P::V &ar, const typename P::V &ai, const typename P::V &br,
+                                     const typename P::V &bi, typename P::V &cr, typename P::V &ci, E &g)
 {
-    typename P::V n2 = P::add(P::mul(br, br), P::mul(bi, bi));
-    typename P::V r = vrecip<P>(n2);
+    typename P::V n2 = P::add(P::mul(br, br, g), P::mul(bi, bi, g), g);
+    typename P::V r = vrecip<P>(n2, g);
     typename P::V tr, ti;
-    cmul<P>(ar, ai, br, vneg<P>(bi), tr, ti);
-    cr = P::mul(tr, r);
-    ci = P::mul(ti, r);
+    cmul<P>(ar, ai, br, vneg<P>(bi), tr, ti, g);
+    cr = P::mul(tr, r, g);
+    ci = P::mul(ti, r, g);
+}
+
+template <class P>
+__device__ __forceinline__ void cdiv(const typename P::V &ar, const typename P::V &ai, const typename P::V &br,
+                                     const typename P::V &bi, typename P::V &cr, typename P::V &ci)
+{
+    NativeEngine<typename P::T> g;
+    cdiv<P>(ar, ai, br, bi, cr, ci, g);
 }
 
 }  // namespace mp
