@@ -417,6 +417,16 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
            "root_sweeps_per_s": float(np.sum(prob.degrees * it)) / tb,
            "fp64_instr_per_s": instr / tb, "fp64_instr_frac": instr / tb / peak,
            "status_counts": np.bincount(st, minlength=5).tolist()}
+    # the same replay with the hybrid engine (opts.engine = 1): same bits, time for comparison
+    gh = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=sweeps, sort=1, engine=1)
+    e0.record()
+    rh, ith, _ = gh.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    res["hybrid_engine_graph_s"] = e0.elapsed_time(e1) / 1e3
+    res["hybrid_engine_identical_bits"] = bool(torch.equal(rh.view(torch.int64), g.roots.view(torch.int64)) and
+                                               np.array_equal(ith.cpu().numpy(), it))
+    del gh
     order = np.argsort(prob.degrees, kind="stable")
     sel = order[np.linspace(0, npoly - 1, loop_polys).astype(int)]
     hc = coef.cpu().numpy()

@@ -54,7 +54,7 @@ class RootsOpts(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("radius", ctypes.c_double),
                 ("watchdog_cycles", ctypes.c_int64), ("max_degree", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("sort", ctypes.c_int32)]
+                ("sort", ctypes.c_int32), ("engine", ctypes.c_int32)]
 
 
 def _declare(L):
@@ -417,7 +417,7 @@ def roots_max_degree(prec):
 
 def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_window=0,
           stag_min_iter=0, mode=0, radius=0.0, watchdog_cycles=0, threads=0, blocks_per_sm=0,
-          sort=0, out=None, ws=None):
+          sort=0, out=None, ws=None, engine=0):
     """Durand-Kerner on every polynomial; returns (roots (2K, total), iters, status)."""
     t = _torch()
     _check(prec, coef, "coef", 2)
@@ -432,7 +432,7 @@ def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_w
     if ws is None:
         ws = t.empty(max(nb, 1), dtype=t.uint8, device=dev)
     o = RootsOpts(tol, max_iter, stag_window, stag_min_iter, mode, radius, watchdog_cycles,
-                  int(max_degree), threads, blocks_per_sm, sort)
+                  int(max_degree), threads, blocks_per_sm, sort, engine)
     _call(f"mp_roots_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), _ptr(z0),
           z0.stride(0) if z0 is not None else 0, _ptr(r), r.stride(0), _ptr(iters),
           _ptr(status), ctypes.byref(o), _ptr(ws), ws.numel(), _stream())
@@ -447,7 +447,7 @@ class RootsGraph:
 
     def __init__(self, prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0,
                  stag_window=0, stag_min_iter=0, radius=0.0, watchdog_cycles=0, threads=0,
-                 blocks_per_sm=0, sort=1):
+                 blocks_per_sm=0, sort=1, engine=0):
         t = _torch()
         _check(prec, coef, "coef", 2)
         K = PRECS[prec][0]
@@ -460,11 +460,11 @@ class RootsGraph:
         self.status = t.zeros(self.npoly, dtype=t.int32, device=dev)
         self.ws = t.empty(max(roots_workspace(prec, self.npoly), 1), dtype=t.uint8, device=dev)
         self.opts = RootsOpts(tol, max_iter, stag_window, stag_min_iter, 0, radius, watchdog_cycles,
-                              int(max_degree), threads, blocks_per_sm, sort)
+                              int(max_degree), threads, blocks_per_sm, sort, engine)
         # one single-sweep launch outside capture loads the module and sets the
         # kernel's attributes; the captured launch then runs the full options
         warm = RootsOpts(tol, 1, stag_window, stag_min_iter, 0, radius, watchdog_cycles,
-                         int(max_degree), threads, blocks_per_sm, sort)
+                         int(max_degree), threads, blocks_per_sm, sort, engine)
         self._launch(warm)
         t.cuda.synchronize()
         self.graph = t.cuda.CUDAGraph()

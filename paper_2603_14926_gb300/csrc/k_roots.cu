@@ -290,7 +290,7 @@ __device__ __noinline__ void dk_update_native(int64_t i, int64_t n, const double
     dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, nat);
 }
 
-template <class P>
+template <class P, class E>
 __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *smem)
 {
     using V = typename P::V;
@@ -383,7 +383,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
         for (int64_t i = tid; i < n; i += nt) {
             const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
             V yr, yi, wr, wi;
-            FastEngine<P> g;
+            E g;
             dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
             if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
             vstore<P>(zn, pn, i, yr);
@@ -425,8 +425,18 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     __syncthreads();
 }
 
-template <class P>
-__global__ void __launch_bounds__(256, 2) k_dk_persistent(DKArgs<P> A)
+// Register budgets: the native engine at its natural size (3 blocks of 128
+// threads per SM fit), the hybrid engine capped at 128 so that 2 blocks of 256
+// threads stay resident (its integer dependency chains need the warps).
+template <class E> struct DKLaunch {
+    static constexpr int min_blocks = 0, default_threads = 128;
+};
+template <bool Q> struct DKLaunch<HybridEngine<Q>> {
+    static constexpr int min_blocks = 2, default_threads = 256;
+};
+
+template <class P, class E>
+__global__ void __launch_bounds__(256, DKLaunch<E>::min_blocks) k_dk_persistent(DKArgs<P> A)
 {
     extern __shared__ __align__(16) double dk_smem[];
     __shared__ DKShared sh;
@@ -437,16 +447,16 @@ __global__ void __launch_bounds__(256, 2) k_dk_persistent(DKArgs<P> A)
         const int64_t p = next;
         __syncthreads();
         if (p >= A.npoly) break;
-        dk_solve<P>(A, A.order ? A.order[p] : p, sh, dk_smem);
+        dk_solve<P, E>(A, A.order ? A.order[p] : p, sh, dk_smem);
     }
 }
 
-template <class P>
-__global__ void __launch_bounds__(256, 2) k_dk_single(DKArgs<P> A, int64_t p)
+template <class P, class E>
+__global__ void __launch_bounds__(256, DKLaunch<E>::min_blocks) k_dk_single(DKArgs<P> A, int64_t p)
 {
     extern __shared__ __align__(16) double dk_smem[];
     __shared__ DKShared sh;
-    dk_solve<P>(A, A.order ? A.order[p] : p, sh, dk_smem);
+    dk_solve<P, E>(A, A.order ? A.order[p] : p, sh, dk_smem);
 }
 
 // Descending-degree order (ties by index): order[rank(p)] = p.
@@ -498,7 +508,7 @@ __global__ void __launch_bounds__(256) k_dk_start(int64_t npoly, const int64_t *
     A.watchdog = 0;
     A.max_degree = max_degree;
     A.order = nullptr;
-    for (int64_t b = blockIdx.x; b < npoly; b += gridDim.x) dk_solve<P>(A, b, sh, dk_smem);
+    for (int64_t b = blockIdx.x; b < npoly; b += gridDim.x) dk_solve<P, NativeEngine<double>>(A, b, sh, dk_smem);
 }
 
 template <class P> static size_t dk_smem_bytes(int32_t max_degree)
@@ -515,6 +525,38 @@ template <class P> static int32_t dk_max_degree()
 
 static size_t dk_ws(int64_t npoly) { return 256 + (size_t)(npoly > 0 ? npoly : 0) * sizeof(int32_t); }
 
+// The persistent batched launch (mode 0) or one launch per polynomial (mode 1).
+template <class P, class E>
+static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npoly, int threads, size_t smem,
+                        cudaStream_t st)
+{
+    if (o->mode == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_dk_persistent<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        int per_sm = o->blocks_per_sm;
+        if (per_sm <= 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dk_persistent<P, E>, threads, smem);
+            if (e != cudaSuccess) return cuda_status(e);
+            if (per_sm < 1) per_sm = 1;
+        }
+        int64_t grid = (int64_t)sm_count() * per_sm;
+        if (grid > npoly) grid = npoly;
+        e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_status(e);
+        k_dk_persistent<P, E><<<(unsigned)grid, threads, smem, st>>>(A);
+        return launch_status();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_dk_single<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int64_t p = 0; p < npoly; p++) {
+        k_dk_single<P, E><<<1, threads, smem, st>>>(A, p);
+        mp_status r = launch_status();
+        if (r != MP_OK) return r;
+    }
+    return MP_OK;
+}
+
 template <class P>
 static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,
                               const double *z0, int64_t pz0, double *roots, int64_t proots, int32_t *iters,
@@ -527,7 +569,10 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         return MP_EINVAL;
     if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
     if (o->mode != 0 && o->mode != 1) return MP_EINVAL;
-    const int threads = o->threads > 0 ? o->threads : 256;
+    if (o->engine != 0 && o->engine != 1) return MP_EINVAL;
+    const int threads = o->threads > 0 ? o->threads
+                                       : (o->engine == 1 ? DKLaunch<HybridEngine<false>>::default_threads
+                                                         : DKLaunch<NativeEngine<double>>::default_threads);
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
     if (ws == nullptr) return MP_EINVAL;
@@ -561,31 +606,8 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         if (e != MP_OK) return e;
         A.order = order;
     }
-    if (o->mode == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_dk_persistent<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return cuda_status(e);
-        int per_sm = o->blocks_per_sm;
-        if (per_sm <= 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dk_persistent<P>, threads, smem);
-            if (e != cudaSuccess) return cuda_status(e);
-            if (per_sm < 1) per_sm = 1;
-        }
-        int64_t grid = (int64_t)sm_count() * per_sm;
-        if (grid > npoly) grid = npoly;
-        e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
-        if (e != cudaSuccess) return cuda_status(e);
-        k_dk_persistent<P><<<(unsigned)grid, threads, smem, st>>>(A);
-        return launch_status();
-    }
-    cudaError_t e = cudaFuncSetAttribute(k_dk_single<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_status(e);
-    for (int64_t p = 0; p < npoly; p++) {
-        k_dk_single<P><<<1, threads, smem, st>>>(A, p);
-        mp_status r = launch_status();
-        if (r != MP_OK) return r;
-    }
-    return MP_OK;
+    return o->engine == 1 ? dk_run<P, HybridEngine<false>>(A, o, npoly, threads, smem, st)
+                          : dk_run<P, NativeEngine<double>>(A, o, npoly, threads, smem, st);
 }
 
 template <class P>

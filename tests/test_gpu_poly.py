@@ -122,24 +122,50 @@ def _solve_both(mp, oracle, prec, prob, coef, **kw):
 
 
 @pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
-def test_roots_bit_exact(mp, oracle, prec):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_roots_bit_exact(mp, oracle, prec, engine):
     prob = inputs.dk_problem(3, 6, 10, 40)
     coef = oracle.poly_from_roots(prec, prob)
-    (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, prob, coef)
+    (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, prob, coef, engine=engine)
     assert np.array_equal(it, wit) and np.array_equal(st, wst)
     assert same_bits(np.ascontiguousarray(r), wr)
     assert np.all((st == 1) | (st == 2))
 
 
-@pytest.mark.parametrize("mode,sort,threads", [(0, 0, 64), (0, 1, 256), (1, 0, 128), (1, 1, 32)])
-def test_roots_modes_identical(mp, oracle, mode, sort, threads):
+@pytest.mark.parametrize("prec", ["dd", "td", "qd"])
+def test_roots_range_limits_bit_exact(mp, oracle, prec):
+    """Hybrid engine (opts.engine = 1).  One starting value per polynomial placed
+    near 2^-1000 makes the first sweep's Horner products leave the hybrid engine's
+    domain (subnormal error terms): that root is recomputed on the FP64 pipe, and roots, sweep counts and
+    statuses stay bit-identical to the oracle.  (Two such starting values would
+    make a difference underflow to zero and the solve break down.)"""
+    K = oracle.PRECS[prec][0]
+    prob = inputs.dk_problem(5, 4, 12, 30)
+    coef = oracle.poly_from_roots(prec, prob)
+    z0 = np.zeros((2 * K, int(prob.degrees.sum())))
+    for b in range(prob.npoly):
+        c = coef[:, prob.coef_off[b]:prob.coef_off[b + 1]]
+        z = oracle.aberth(prec, c, radius=1.1)
+        z[:, :1] *= 2.0 ** -1000
+        z0[:, prob.root_off[b]:prob.root_off[b + 1]] = z
+    r, it, st = mp.roots(prec, dev(prob.coef_off), dev(coef), int(prob.degrees.max()), z0=dev(z0), max_iter=40,
+                         engine=1)
+    wr, wit, wst = oracle.roots(prec, prob.coef_off, coef, z0=z0, max_iter=40)
+    assert np.array_equal(host(it), wit) and np.array_equal(host(st), wst)
+    assert np.isfinite(wr).all() and np.all(wst != 4)
+    assert same_bits(np.ascontiguousarray(host(r)), wr)
+
+
+@pytest.mark.parametrize("mode,sort,threads,engine", [(0, 0, 64, 0), (0, 1, 256, 0), (1, 0, 128, 0), (1, 1, 32, 0),
+                                                      (0, 1, 256, 1), (1, 0, 64, 1)])
+def test_roots_modes_identical(mp, oracle, mode, sort, threads, engine):
     """Persistent batched launch and the per-polynomial launch loop, sorted or not,
     any block size: identical bits, equal to the oracle."""
     prec = "td"
     prob = inputs.dk_problem(8, 9, 3, 70)
     coef = oracle.poly_from_roots(prec, prob)
     (r, it, st), (wr, wit, wst) = _solve_both(mp, oracle, prec, prob, coef, mode=mode, sort=sort,
-                                              threads=threads, radius=1.1)
+                                              threads=threads, radius=1.1, engine=engine)
     assert np.array_equal(it, wit) and np.array_equal(st, wst)
     assert same_bits(np.ascontiguousarray(r), wr)
 
