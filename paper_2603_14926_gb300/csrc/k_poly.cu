@@ -9,25 +9,26 @@
 // Adjoint, dy -> (dcoef, dx):
 //   dx: one thread per point, simultaneous Horner recurrence for p'.
 //   dcoef_i = sum over points m (ascending) of dy_m x_m^i.  One warp per
-//   polynomial sweeps blocks of 32 coefficients as a wavefront: lane L owns
-//   coefficient 32j+L and at step s handles point m = s - L, receiving
-//   dy_m x_m^(i-1) * x_m from lane L-1 through a register shuffle.  Each
-//   coefficient is therefore folded over the points in ascending order with the
-//   powers formed by repeated multiplication -- the oracle's order, so the
-//   result is bit-identical -- while all 32 lanes do useful work in all but 31
-//   of npts + 31 steps.  Lane 31 hands the running powers of the next block
-//   (dy_m x_m^(32(j+1))) to the next sweep through a per-point workspace.
+//   polynomial sweeps the coefficients as a wavefront, DCOEF_DEPTH blocks of 32
+//   per pass: lane L owns coefficient i = j0 + 32d + L and at step s handles
+//   point m = s - 32d - L, receiving dy_m x_m^(i-1) * x_m from the coefficient
+//   before it (lane L-1, or lane 31 of block d-1) through a register shuffle.
+//   Each coefficient is therefore folded over the points in ascending order
+//   with the powers formed by repeated multiplication -- the oracle's order, so
+//   the result is bit-identical.  The last block's lane 31 hands the running
+//   powers of the next pass over through a per-point workspace.
 //
 // Polynomials from roots: one block per polynomial, the coefficient vector in
 // shared memory, one factor (x - r) or (x^2 + Bx + C) per synchronised stage,
 // all coefficients of a stage in parallel.
 //
-// Evaluation and the adjoint run on FastEngine<P> (binary64: TwoSum's error
-// term on the integer pipes).  A point whose integer path left its domain is
-// recomputed with the FP64 pipe; the coefficient wavefront, whose lanes pass
-// values to each other and to the next sweep, restarts the whole polynomial
-// on the FP64 pipe when any lane of the warp failed.  Every result is the FP64
-// sequence's bits.
+// Evaluation and dx run on FastEngine<P> (binary64: TwoSum's error term on the
+// integer pipes); a point whose integer path left its domain is recomputed
+// with the FP64 pipe, so every result is the FP64 sequence's bits.  The
+// coefficient wavefront runs on the FP64 pipe (see k_poly_dcoef); its sweep
+// routine also takes a failing engine, restarting the whole polynomial on the
+// FP64 pipe when any lane of the warp failed, because its lanes pass values to
+// each other and to the next pass.
 #include <cuda_runtime.h>
 
 #include "mp_arith.cuh"
@@ -173,9 +174,16 @@ __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *_
 
 constexpr int DCOEF_WARPS = 4;
 
-// All coefficient sweeps of one polynomial (one warp).  Returns true, after the
-// sweep in which it happened, when any lane's engine failed; the caller then
-// starts again from the first sweep (dy is never overwritten) on the FP64 pipe.
+// Coefficient blocks per warp pass.  Lane L holds coefficients j0 + 32d + L for
+// d = 0..DCOEF_DEPTH-1; block d trails block d-1 by 32 points, so block d's lane 0
+// takes the running power from block d-1's lane 31 one step later through the
+// same rotation shuffle.  Depths 1-4 measured the same (537.6 ms on 1024
+// polynomials x degree 256 x 4096 points): the wavefront is FP64-pipe bound.
+constexpr int DCOEF_DEPTH = 1;
+
+// All coefficient passes of one polynomial (one warp).  Returns true, after the
+// pass in which it happened, when any lane's engine failed; the caller then
+// starts again from the first pass (dy is never overwritten) on the FP64 pipe.
 template <class P, class E>
 __device__ __forceinline__ bool dcoef_sweeps(int64_t n, int64_t off, int64_t base, int64_t npts,
                                              const typename P::T *__restrict__ x, int64_t px,
@@ -184,27 +192,43 @@ __device__ __forceinline__ bool dcoef_sweeps(int64_t n, int64_t off, int64_t bas
                                              typename P::T *__restrict__ wbuf, int64_t pw, E &g)
 {
     using V = typename P::V;
+    constexpr int D = DCOEF_DEPTH;
     const int lane = threadIdx.x & 31;
-    for (int64_t j0 = 0; j0 <= n; j0 += 32) {
-        const int64_t i = j0 + lane;
-        V S = vzero<P>();
-        V win = vzero<P>();
-        for (int64_t s = 0; s < npts + 31; s++) {
-            const int64_t m = s - lane;
-            const bool act = m >= 0 && m < npts && i <= n;
-            V w = win;
-            if (lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
-            V wout = vzero<P>();
-            if (act) {
-                S = P::add(S, w, g);
-                if (i < n) wout = P::mul(w, vload<P>(x, px, base + m), g);
-            }
-            if (lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout);
+    for (int64_t j0 = 0; j0 <= n; j0 += 32 * D) {
+        V S[D], win[D];
 #pragma unroll
-            for (int c = 0; c < P::K; c++) win.c[c] = __shfl_up_sync(0xffffffffu, wout.c[c], 1);
+        for (int d = 0; d < D; d++) S[d] = win[d] = vzero<P>();
+        const int64_t last = npts + 32 * D - 1;  // steps until the last block's lane 31 is done
+        for (int64_t s = 0; s < last; s++) {
+            V wout[D];
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                const int64_t i = j0 + 32 * d + lane, m = s - 32 * d - lane;
+                const bool act = m >= 0 && m < npts && i <= n;
+                V w = win[d];
+                if (d == 0 && lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
+                wout[d] = vzero<P>();
+                if (act) {
+                    S[d] = P::add(S[d], w, g);
+                    if (i < n) wout[d] = P::mul(w, vload<P>(x, px, base + m), g);
+                }
+                if (d == D - 1 && lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout[d]);
+            }
+            // lane L receives lane L-1's outputs; lane 0 of block d takes block d-1's lane 31
+            V r[D];
+#pragma unroll
+            for (int d = 0; d < D; d++)
+#pragma unroll
+                for (int c = 0; c < P::K; c++) r[d].c[c] = __shfl_sync(0xffffffffu, wout[d].c[c], (lane + 31) & 31);
+#pragma unroll
+            for (int d = 0; d < D; d++) win[d] = lane == 0 ? (d > 0 ? r[d - 1] : vzero<P>()) : r[d];
         }
         if (__any_sync(0xffffffffu, g.failed())) return true;
-        if (i <= n) vstore<P>(dcoef, pdc, off + i, S);
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+            const int64_t i = j0 + 32 * d + lane;
+            if (i <= n) vstore<P>(dcoef, pdc, off + i, S[d]);
+        }
         __syncwarp();
     }
     return false;
@@ -225,7 +249,11 @@ __global__ void __launch_bounds__(32 * DCOEF_WARPS)
     const int64_t n = coef_off[b + 1] - off - 1;
     if (n < 0) return;
     const int64_t base = b * npts;  // this polynomial's points
-    FastEngine<P> g;
+    // On the FP64 pipe: at one warp per polynomial the adjoint workload keeps too
+    // few warps per SM to hide the hybrid engine's integer latency (hybrid: 632 ms,
+    // FP64 pipe: 538 ms = 88% of the pipe bound, same bits).  The restart path
+    // serves engines that can fail.
+    NativeEngine<typename P::T> g;
     if (dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, g)) {
         NativeEngine<typename P::T> nat;
         dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, nat);

@@ -38,11 +38,13 @@ def test_polyeval_bit_exact(mp, oracle, prec):
 
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
-@pytest.mark.parametrize("npts", [1, 77])
-def test_polyeval_backward_bit_exact(mp, oracle, prec, npts):
-    """Degrees 0..70 span three 32-coefficient sweeps of the wavefront."""
+@pytest.mark.parametrize("npts", [0, 1, 77])
+@pytest.mark.parametrize("dmax", [70, 200])
+def test_polyeval_backward_bit_exact(mp, oracle, prec, npts, dmax):
+    """Degrees 0..70 fit one pass of the wavefront (three blocks of 32 coefficients);
+    degrees up to 200 take three passes chained through the workspace."""
     K, dt = oracle.PRECS[prec]
-    off, coef = ragged(4, 7, 0, 70, K, dt)
+    off, coef = ragged(4, 7, 0 if dmax == 70 else 90, dmax, K, dt)
     off[2] = off[1]  # an empty polynomial (no coefficients)
     npoly = len(off) - 1
     x = inputs.mp_uniform(5, npoly * npts, K, dt, stream=inputs.STREAM_X)
