@@ -155,6 +155,13 @@ double mpref_dk_nthroot(double v, int64_t m) { return dk_nthroot(v, m); }
         MPREF_CAT(polyeval, SFXV)(&PV, npoly, coef_off, coef, pcoef, npts, x_re, x_im, px,   \
                                   y_re, y_im, py);                                          \
     }                                                                                       \
+    void mpref_polyeval_estrin_##S(int64_t npoly, const int64_t *coef_off, const T *coef,   \
+                                   int64_t pcoef, int64_t npts, const T *x_re, const T *x_im, \
+                                   int64_t px, T *y_re, T *y_im, int64_t py)                \
+    {                                                                                       \
+        MPREF_CAT(polyeval_estrin, SFXV)(&PV, npoly, coef_off, coef, pcoef, npts, x_re, x_im, \
+                                         px, y_re, y_im, py);                               \
+    }                                                                                       \
     void mpref_polyeval_backward_##S(int64_t npoly, const int64_t *coef_off, const T *coef, \
                                      int64_t pcoef, int64_t npts, const T *x, int64_t px,   \
                                      const T *dy, int64_t pdy, T *dcoef, int64_t pdc,       \

@@ -130,6 +130,7 @@ def _declare(L):
             "cgemm": [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp,
                       _i64, _i64, _vp, _vp, _i64, _i64],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64],
+            "polyeval_estrin": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                   _vp, _i64],
         }
@@ -310,6 +311,22 @@ def polyeval(prec, coef_off, coef, npts, x_re, x_im=None):
     getattr(lib(), f"mpref_polyeval_{prec}")(npoly, _p(off), _p(coef), coef.shape[1], npts,
                                              _p(x_re), _p(x_im), x_re.shape[1], _p(y_re),
                                              _p(y_im), y_re.shape[1])
+    return (y_re, y_im) if x_im is not None else y_re
+
+
+def polyeval_estrin(prec, coef_off, coef, npts, x_re, x_im=None):
+    """Batched evaluation by Estrin's scheme (same layout and returns as polyeval)."""
+    coef = _arr(coef, prec)
+    off = np.ascontiguousarray(coef_off, dtype=np.int64)
+    npoly = len(off) - 1
+    x_re = _arr(x_re, prec)
+    x_im = _arr(x_im, prec) if x_im is not None else None
+    K = coef.shape[0]
+    y_re = np.zeros((K, npoly * npts), dtype=coef.dtype)
+    y_im = np.zeros_like(y_re) if x_im is not None else None
+    getattr(lib(), f"mpref_polyeval_estrin_{prec}")(npoly, _p(off), _p(coef), coef.shape[1], npts,
+                                                    _p(x_re), _p(x_im), x_re.shape[1], _p(y_re),
+                                                    _p(y_im), y_re.shape[1])
     return (y_re, y_im) if x_im is not None else y_re
 
 

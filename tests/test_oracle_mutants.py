@@ -4,7 +4,8 @@ that its pins catch every one.
 Each mutant edits one line of the oracle's C source: a wrong operand, TwoSum
 swapped for QuickTwoSum, a dropped term, a swapped component index, a sign
 slip, transposed GEMM indices, an off-by-one Horner coefficient, a Newton sign
-error, a Durand-Kerner product that includes j = i.  The pin battery below
+error, a Durand-Kerner product that includes j = i, a mis-wired Estrin tree.
+The pin battery below
 (exact rationals, the op counts of Tables 1 and 2, error bounds, identities,
 permutation GEMM, known roots) must pass on the real oracle and fail on every
 mutant.
@@ -50,6 +51,11 @@ MUTANTS = [
     ("Horner off-by-one", CORE, "        F(load)(P, coef, pc, i, a);\n        P->mul(h, x, h);",
      "        F(load)(P, coef, pc, i + 1, a);\n        P->mul(h, x, h);"),
     ("Newton sign", CORE, "        F(mp_sub)(P, one, t, e);", "        F(mp_sub)(P, t, one, e);"),
+    ("Estrin lo/hi swapped", CORE, "                P->mul(hi_r, pr, t1);\n                P->add(t1, lo_r, vr + 4 * j);",
+     "                P->mul(lo_r, pr, t1);\n                P->add(t1, hi_r, vr + 4 * j);"),
+    ("Estrin lost pass-through", CORE, "                vr[4 * half + c] = vr[4 * (len - 1) + c];",
+     "                vr[4 * half + c] = 0;"),
+    ("Estrin power doubled, not squared", CORE, "                P->mul(pr, pr, pr);", "                P->add(pr, pr, pr);"),
     ("DK product includes j == i", DK, "                if (j == i) continue;\n                load_d(P, z, pz, j, zjr);",
      "                load_d(P, z, pz, j, zjr);"),
     ("DK wrong update sign", DK, "            mp_sub_d(P, zr, wr, yr);", "            P->add(zr, wr, yr);"),
@@ -156,6 +162,17 @@ def _blas_poly(oracle, bad):
         x = mp_value(xv[:, m])
         ex = sum(cv[i] * x ** i for i in range(9))
         check("Horner vs exact", abs(mp_value(y[:, m]) - ex) <= Fraction(2) ** -200)
+    # Estrin on exactly representable cases (integer coefficients, x = 2 and -3/2)
+    rng = np.random.default_rng(11)
+    for n in (4, 5, 6, 7, 12):
+        a = rng.integers(-15, 16, n + 1)
+        cf = np.zeros((K, n + 1))
+        cf[0] = a
+        for xq in (Fraction(2), Fraction(-3, 2)):
+            xe = np.zeros((K, 1))
+            xe[0, 0] = float(xq)
+            ye = oracle.polyeval_estrin("qd", np.array([0, n + 1], dtype=np.int64), cf, 1, xe)
+            check("Estrin exact", mp_value(ye[:, 0]) == sum(int(a[i]) * xq ** i for i in range(n + 1)))
     # reciprocal
     r = oracle.recip("qd", xv)
     for v, w in zip(mp_values(xv), mp_values(r)):

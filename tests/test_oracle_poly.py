@@ -78,6 +78,95 @@ def test_horner_real_and_complex_vs_exact(oracle, prec):
 
 
 # ---------------------------------------------------------------------------
+# Estrin
+# ---------------------------------------------------------------------------
+
+def _estrin_exact_cases(prec, dt):
+    """(n, a, x) with small integer coefficients where every value any evaluation
+    order forms is exactly representable in one component of the type."""
+    bits = 50 if dt == np.float64 else 22
+    rng = np.random.default_rng(7)
+    for n in range(0, 41):
+        a = [int(v) for v in rng.integers(-15, 16, n + 1)]
+        for x in (Fraction(2), Fraction(-2), Fraction(1, 2), Fraction(-3, 2)):
+            # numerators over the common denominator stay below 2^bits
+            num = 15 * sum(abs(x.numerator) ** i * x.denominator ** (n - i) for i in range(n + 1))
+            top = abs(x.numerator) ** (1 << max(0, (n).bit_length()))
+            if num < 2 ** bits and top < 2 ** bits:
+                yield n, a, x
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
+def test_estrin_exact_on_representable_cases(oracle, prec):
+    """Integer coefficients at x in {2, -2, 1/2, -3/2} (and x = 1 + i below): every
+    intermediate of any order is exact, so the result must be the exact value.  A
+    wrong pairing, power or pass-through of the tree changes it."""
+    K, dt = oracle.PRECS[prec]
+    count = 0
+    for n, a, x in _estrin_exact_cases(prec, dt):
+        cf = np.zeros((K, n + 1), dtype=dt)
+        cf[0] = a
+        xe = np.zeros((K, 1), dtype=dt)
+        xe[0, 0] = float(x)
+        y = oracle.polyeval_estrin(prec, np.array([0, n + 1], dtype=np.int64), cf, 1, xe)
+        assert mp_value(y[:, 0]) == sum(a[i] * x ** i for i in range(n + 1)), (n, x)
+        count += 1
+    assert count > 40
+    # complex argument 1 + i: Gaussian integers
+    for n in range(0, 21 if dt == np.float64 else 9):
+        a = [int(v) for v in np.random.default_rng(n).integers(-15, 16, n + 1)]
+        cf = np.zeros((K, n + 1), dtype=dt)
+        cf[0] = a
+        one = np.zeros((K, 1), dtype=dt)
+        one[0, 0] = 1.0
+        yr, yi = oracle.polyeval_estrin(prec, np.array([0, n + 1], dtype=np.int64), cf, 1, one, one)
+        h = (Fraction(0), Fraction(0))
+        for i in range(n, -1, -1):
+            h = cmul(h, (Fraction(1), Fraction(1)))
+            h = (h[0] + a[i], h[1])
+        assert (mp_value(yr[:, 0]), mp_value(yi[:, 0])) == h, n
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
+def test_estrin_vs_exact_and_horner(oracle, prec):
+    """Random coefficients and points: within the evaluation bound of the exact
+    value (real and complex arguments); degrees 0 and 1 equal Horner bit for bit
+    (the same single operation)."""
+    K, dt = oracle.PRECS[prec]
+    p = K * (53 if dt == np.float64 else 24)
+    npts = 5
+    off, coef = poly_problem(21, 7, 0, 40, K, dt)
+    npoly = len(off) - 1
+    xr = inputs.mp_uniform(22, npoly * npts, K, dt, stream=inputs.STREAM_X)
+    xi = inputs.mp_uniform(23, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    yr = oracle.polyeval_estrin(prec, off, coef, npts, xr)
+    cr, ci = oracle.polyeval_estrin(prec, off, coef, npts, xr, xi)
+    cv = mp_values(coef)
+    for b in range(npoly):
+        a = cv[off[b]:off[b + 1]]
+        n = len(a) - 1
+        for m in range(npts):
+            idx = b * npts + m
+            x = mp_value(xr[:, idx])
+            z = (x, mp_value(xi[:, idx]))
+            ex = sum(a[i] * x ** i for i in range(n + 1))
+            mag = sum(abs(a[i]) * abs(x) ** i for i in range(n + 1))
+            assert abs(mp_value(yr[:, idx]) - ex) <= Fraction(8 * n + 16) * Fraction(2) ** -p * mag
+            h = (Fraction(0), Fraction(0))
+            for i in range(n, -1, -1):
+                h = cmul(h, z)
+                h = (h[0] + a[i], h[1])
+            zabs = abs(complex(float(z[0]), float(z[1])))
+            bc = (16 * n + 16) * 2.0 ** -p * sum(abs(float(a[i])) * zabs ** i for i in range(n + 1))
+            assert float(abs(mp_value(cr[:, idx]) - h[0])) <= bc
+            assert float(abs(mp_value(ci[:, idx]) - h[1])) <= bc
+    low = np.array([0, 1, 3, 4], dtype=np.int64)  # degrees 0, 1, 0
+    cl = inputs.mp_uniform(24, 4, K, dt, stream=inputs.STREAM_C)
+    xl = inputs.mp_uniform(25, 3 * npts, K, dt, stream=inputs.STREAM_X)
+    assert np.array_equal(oracle.polyeval_estrin(prec, low, cl, npts, xl), oracle.polyeval(prec, low, cl, npts, xl))
+
+
+# ---------------------------------------------------------------------------
 # Adjoint of Horner evaluation
 # ---------------------------------------------------------------------------
 
