@@ -317,8 +317,9 @@ def extras(prec="qd", quick=False):
     def rates(fp64, paper, t):
         return {"fp64_instr_frac": fp64 / t / peak, "paper_sequence_equiv_frac": paper / t / peak}
 
-    def timed(fn, reps=3):
-        fn()
+    def timed(fn, reps=3, warm=True):
+        if warm:
+            fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -369,12 +370,68 @@ def extras(prec="qd", quick=False):
     steps = npoly * npts * deg
     out["horner_fwd"] = {"polys": npoly, "degree": deg, "points": npts, "ms": t * 1e3,
                          **rates(steps * ins, steps * ins_paper, t)}
+    # Estrin's scheme (Section 4.1) on the same workload: n multiply-add pairs plus
+    # ceil(log2(n+1)) - 1 squarings per point, against Horner's n pairs
+    te = timed(lambda: mpg.polyeval(prec, off, coef, npts, xs, scheme="estrin"), reps=1)
+    lev = int(np.ceil(np.log2(deg + 1)))
+    est_fp64 = npoly * npts * (deg * ins + (lev - 1) * mul_instr(prec))
+    est_paper = npoly * npts * (deg * ins_paper + (lev - 1) * INSTR_MUL[prec])
+    out["estrin_fwd"] = {"ms": te * 1e3, "vs_horner": te / t, **rates(est_fp64, est_paper, te)}
+    # latency case: one polynomial of degree 256 at 64 points (one block)
+    off1, c1, x1 = off[:2].contiguous(), coef[:, :deg + 1].contiguous(), xs[:, :64].contiguous()
+    th1 = timed(lambda: mpg.polyeval(prec, off1, c1, 64, x1), reps=5)
+    te1 = timed(lambda: mpg.polyeval(prec, off1, c1, 64, x1, scheme="estrin"), reps=5)
+    out["estrin_latency_one_poly_64_points"] = {"horner_ms": th1 * 1e3, "estrin_ms": te1 * 1e3,
+                                                "estrin_over_horner": te1 / th1}
     wsb = torch.empty(mpg.polyeval_backward_workspace(prec, npoly, npts), dtype=torch.uint8, device="cuda")
     tb = timed(lambda: mpg.polyeval_backward(prec, off, coef, npts, xs, dy, ws=wsb), reps=1)
     # dx: 2 mul + 2 add per step (+1 mul), dcoef: 1 mul + 1 add per (coefficient, point)
-    bw = lambda i, mu: steps * 2 * i + npoly * npts * mu + npoly * npts * (deg + 1) * i  # noqa: E731
+    # dx on the hybrid engine; the coefficient wavefront on the FP64 pipe
+    bw = lambda i, mu, ic: steps * 2 * i + npoly * npts * mu + npoly * npts * (deg + 1) * ic  # noqa: E731
     out["horner_bwd"] = {"ms": tb * 1e3, "vs_fwd": tb / t,
-                         **rates(bw(ins, mul_instr(prec)), bw(ins_paper, INSTR_MUL[prec]), tb)}
+                         **rates(bw(ins, mul_instr(prec), ins_paper), bw(ins_paper, INSTR_MUL[prec], ins_paper), tb)}
+    del off, coef, xs, dy, wsb
+    # GEMM adjoint through torch.autograd.Function: dA = dC B^T, dB = A^T dC
+    from paper_2603_14926_gb300.autograd import mp_gemm
+
+    ng = 1024 if quick else 2048
+    A = dev(inputs.mp_uniform(11, (ng, ng), K)).requires_grad_(True)
+    B = dev(inputs.mp_uniform(12, (ng, ng), K)).requires_grad_(True)
+    dC = dev(inputs.mp_uniform(13, (ng, ng), K))
+    C = mp_gemm(prec, A, B)
+    tf = timed(lambda: mp_gemm(prec, A, B), reps=1)
+    tbk = timed(lambda: torch.autograd.grad(C, (A, B), dC, retain_graph=True), reps=1)
+    out["gemm_backward"] = {"n": ng, "forward_ms": tf * 1e3, "backward_ms": tbk * 1e3, "backward_over_forward": tbk / tf,
+                            "path": "torch.autograd.Function (MPGemm): two transposed-operand GEMMs",
+                            **rates(2 * ng ** 3 * ins, 2 * ng ** 3 * ins_paper, tbk)}
+    del A, B, dC, C
+    # square GEMM across precisions and sizes (built-in configuration; one launch each)
+    sizes = (1024,) if quick else (1024, 2048, 4096)
+    grid = {}
+    for p2 in ("dd", "td", "qd"):
+        K2 = mpg.PRECS[p2][0]
+        for n2 in sizes:
+            A2 = dev(inputs.mp_uniform(2, (n2, n2), K2, stream=inputs.STREAM_A))
+            B2 = dev(inputs.mp_uniform(2, (n2, n2), K2, stream=inputs.STREAM_B))
+            C2 = mpg.empty(p2, n2, n2)
+            # the smallest size warms the precision's kernels; larger ones run once
+            t2 = timed(lambda: mpg.gemm(p2, A2, B2, out=C2), reps=1, warm=n2 == sizes[0])
+            fp64 = n2 ** 3 * (add_instr(p2) + mul_instr(p2))
+            grid[f"{p2}_{n2}"] = {"ms": t2 * 1e3, "mac_per_s": n2 ** 3 / t2,
+                                  **rates(fp64, n2 ** 3 * mac_instr(p2), t2)}
+            del A2, B2, C2
+    fp32_peak = NOMINAL_FP32_TFLOPS * 1e12 / 2
+    for p2 in ("tf", "qf"):
+        K2 = mpg.PRECS[p2][0]
+        n2 = sizes[-1]
+        A2 = dev(inputs.mp_uniform(2, (n2, n2), K2, np.float32, stream=inputs.STREAM_A))
+        B2 = dev(inputs.mp_uniform(2, (n2, n2), K2, np.float32, stream=inputs.STREAM_B))
+        C2 = mpg.empty(p2, n2, n2)
+        t2 = timed(lambda: mpg.gemm(p2, A2, B2, out=C2), reps=1)
+        grid[f"{p2}_{n2}"] = {"ms": t2 * 1e3, "mac_per_s": n2 ** 3 / t2,
+                              "fp32_instr_frac_of_nominal": n2 ** 3 * mac_instr(p2) / t2 / fp32_peak}
+        del A2, B2, C2
+    out["gemm_sizes"] = grid
     return out
 
 

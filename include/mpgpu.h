@@ -192,11 +192,24 @@ const char *mp_version(void);
 /* Real: h = a_n; h = add(mul(h, x), a_i).  Complex (four real products):   */
 /*   re' = add(add(mul(hr,xr), neg(mul(hi,xi))), a_i),                      */
 /*   im' = add(mul(hr,xi), mul(hi,xr)).  Bit-identical to the CPU oracle.   */
+/* mp_polyeval_estrin_P: the same evaluation by Estrin's scheme (Section    */
+/* 4.1 compares it with Horner's; the standard pairwise tree): level 0 holds */
+/* a_0..a_n; each level replaces adjacent pairs (lo, hi) by                   */
+/* add(mul(hi, y_k), lo), y_0 = x, y_{k+1} = mul(y_k, y_k); an unpaired last */
+/* value moves up unchanged.  Complex arguments: every value complex, the    */
+/* products in Horner's 4M order, re = add(sub(mul(hr,yr), mul(hi,yi)), lo), */
+/* im = add(add(mul(hr,yi), mul(hi,yr)), lo_im).  Same arguments as          */
+/* mp_polyeval_P; bit-identical to the CPU oracle.  Degrees up to 2^25 - 1;   */
+/* a polynomial above that evaluates to NaN.                                 */
 /* ------------------------------------------------------------------------ */
 #define MPGPU_DECL_POLY(P, T)                                                               \
     mp_status mp_polyeval_##P(int64_t npoly, const int64_t *coef_off, const T *coef,         \
                               int64_t pcoef, int64_t npts, const T *x_re, const T *x_im,     \
                               int64_t px, T *y_re, T *y_im, int64_t py, mp_stream stream);   \
+    mp_status mp_polyeval_estrin_##P(int64_t npoly, const int64_t *coef_off, const T *coef,  \
+                                     int64_t pcoef, int64_t npts, const T *x_re,             \
+                                     const T *x_im, int64_t px, T *y_re, T *y_im, int64_t py,\
+                                     mp_stream stream);                                      \
     size_t mp_polyeval_backward_workspace_##P(int64_t npoly, int64_t npts);                 \
     mp_status mp_polyeval_backward_##P(int64_t npoly, const int64_t *coef_off, const T *coef,\
                                        int64_t pcoef, int64_t npts, const T *x, int64_t px,  \

@@ -73,6 +73,7 @@ def _declare(L):
             "cgemm": [_int, _int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _i64,
                       _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
+            "polyeval_estrin": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                                   _vp, _i64, _vp, ctypes.c_size_t, _vp],
         }
@@ -348,8 +349,9 @@ def cgemm(prec, Ar, Ai, Br, Bi, opA=0, opB=0, out=None, ws=None):
 # polynomials and roots
 # ---------------------------------------------------------------------------
 
-def polyeval(prec, coef_off, coef, npts, x_re, x_im=None):
-    """Batched Horner; coef_off is a CUDA int64 tensor (npoly+1)."""
+def polyeval(prec, coef_off, coef, npts, x_re, x_im=None, scheme="horner"):
+    """Batched evaluation, Horner's rule (default) or Estrin's scheme
+    (scheme="estrin"); coef_off is a CUDA int64 tensor (npoly+1)."""
     _check(prec, coef, "coef", 2)
     _check(prec, x_re, "x_re", 2)
     npoly = coef_off.numel() - 1
@@ -358,7 +360,10 @@ def polyeval(prec, coef_off, coef, npts, x_re, x_im=None):
     if x_im is not None:
         _check(prec, x_im, "x_im", 2)
         y_im = empty(prec, npoly * npts, device=coef.device)
-    _call(f"mp_polyeval_{prec}", npoly, _ptr(coef_off), _ptr(coef), _ps(coef), npts, _ptr(x_re),
+    if scheme not in ("horner", "estrin"):
+        raise ValueError(f"unknown scheme {scheme!r}")
+    fn = f"mp_polyeval_{prec}" if scheme == "horner" else f"mp_polyeval_estrin_{prec}"
+    _call(fn, npoly, _ptr(coef_off), _ptr(coef), _ps(coef), npts, _ptr(x_re),
           _ptr(x_im), _ps(x_re), _ptr(y_re), _ptr(y_im), _ps(y_re), _stream())
     return (y_re, y_im) if x_im is not None else y_re
 

@@ -123,6 +123,163 @@ static mp_status polyeval_launch(int64_t npoly, const int64_t *coef_off, const t
 }
 
 // ---------------------------------------------------------------------------
+// Estrin's scheme (Section 4.1 compares it with Horner's; the standard pairwise
+// tree): level 0 holds a_0 .. a_n, each level replaces adjacent pairs (lo, hi)
+// by add(mul(hi, y_k), lo) with y_0 = x and y_{k+1} = mul(y_k, y_k), an unpaired
+// last value moves up unchanged.  One thread per point streams the coefficients
+// in ascending order through a binary counter: a new value meets the pending
+// value of each level whose bit is set, as the tree pairs them, and the values
+// still pending at the end are combined from the lowest level up, the lower one
+// as `hi` -- exactly the tree's pass-through rule.  Same operations, same
+// order, same bits as the oracle's level-by-level form.  Pending values and
+// powers live in per-thread (local) arrays; degrees up to 2^(ESTRIN_LEVELS-1)-1.
+// ---------------------------------------------------------------------------
+
+constexpr int ESTRIN_LEVELS = 26;
+
+// (r, i) := (lo_r, lo_i) + (hi_r, hi_i) * (yr, yi), in the order of the 4M
+// complex product of Horner's complex form; real arguments use only r.
+template <class P, bool CPLX, class E>
+__device__ __forceinline__ void estrin_combine(const typename P::V &hr, const typename P::V &hi,
+                                               const typename P::V &lr, const typename P::V &li,
+                                               const typename P::V &yr, const typename P::V &yi,
+                                               typename P::V &rr, typename P::V &ri, E &g)
+{
+    using V = typename P::V;
+    if (!CPLX) {
+        rr = P::add(P::mul(hr, yr, g), lr, g);
+        return;
+    }
+    V t1 = P::mul(hr, yr, g);
+    V t2 = P::mul(hi, yi, g);
+    t1 = vsub<P>(t1, t2, g);
+    V t3 = P::mul(hr, yi, g);
+    V t4 = P::mul(hi, yr, g);
+    t3 = P::add(t3, t4, g);
+    rr = P::add(t1, lr, g);
+    ri = P::add(t3, li, g);
+}
+
+template <class P, bool CPLX, class E>
+__device__ __forceinline__ void estrin_point(int64_t n, const typename P::T *__restrict__ cb, int64_t pc,
+                                             const typename P::V &zr, const typename P::V &zi, typename P::V &outr,
+                                             typename P::V &outi, E &g)
+{
+    using V = typename P::V;
+    V pr[ESTRIN_LEVELS], pi[ESTRIN_LEVELS];  // pending value of each level
+    V yr[ESTRIN_LEVELS], yi[ESTRIN_LEVELS];  // y_k = x^(2^k)
+    int ny = 1;
+    yr[0] = zr;
+    yi[0] = CPLX ? zi : vzero<P>();
+    auto power = [&](int lev) {
+        while (ny <= lev) {
+            const V a = yr[ny - 1], b = yi[ny - 1];
+            if (!CPLX) {
+                yr[ny] = P::mul(a, a, g);
+            } else {
+                V t1 = P::mul(a, a, g);
+                V t2 = P::mul(b, b, g);
+                t1 = vsub<P>(t1, t2, g);
+                V t3 = P::mul(a, b, g);
+                V t4 = P::mul(b, a, g);
+                yi[ny] = P::add(t3, t4, g);
+                yr[ny] = t1;
+            }
+            ny++;
+        }
+    };
+    uint64_t cnt = 0;
+    for (int64_t i = 0; i <= n; i++) {
+        V cr = vload<P>(cb, pc, i), ci = vzero<P>();
+        int lev = 0;
+        while ((cnt >> lev) & 1) {  // pair with the pending value (the lower coefficients) of this level
+            power(lev);
+            V rr, ri;
+            estrin_combine<P, CPLX>(cr, ci, pr[lev], pi[lev], yr[lev], yi[lev], rr, ri, g);
+            cr = rr;
+            ci = ri;
+            lev++;
+        }
+        pr[lev] = cr;
+        pi[lev] = ci;
+        cnt++;
+    }
+    V cr = vzero<P>(), ci = vzero<P>();
+    bool have = false;
+    for (int lev = 0; lev < ESTRIN_LEVELS && (cnt >> lev) != 0; lev++) {
+        if (!((cnt >> lev) & 1)) continue;
+        if (!have) {
+            cr = pr[lev];
+            ci = pi[lev];
+            have = true;
+        } else {
+            power(lev);
+            V rr, ri;
+            estrin_combine<P, CPLX>(cr, ci, pr[lev], pi[lev], yr[lev], yi[lev], rr, ri, g);
+            cr = rr;
+            ci = ri;
+        }
+    }
+    outr = cr;
+    outi = ci;
+}
+
+template <class P, bool CPLX>
+__global__ void __launch_bounds__(256) k_polyeval_estrin(int64_t npoly, const int64_t *__restrict__ coef_off,
+                                                         const typename P::T *__restrict__ coef, int64_t pc,
+                                                         int64_t npts, const typename P::T *__restrict__ xr,
+                                                         const typename P::T *__restrict__ xi, int64_t px,
+                                                         typename P::T *__restrict__ yr,
+                                                         typename P::T *__restrict__ yi, int64_t py)
+{
+    using V = typename P::V;
+    const int64_t total = npoly * npts;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+        const int64_t b = idx / npts;
+        const int64_t off = coef_off[b];
+        const int64_t n = coef_off[b + 1] - off - 1;
+        V hr = vzero<P>(), hi = vzero<P>();
+        if (n >= ((int64_t)1 << (ESTRIN_LEVELS - 1))) {  // beyond the per-thread level arrays: NaN
+            for (int c = 0; c < P::K; c++) hr.c[c] = hi.c[c] = (typename P::T)NAN;
+        } else if (n >= 0) {
+            const V zr = vload<P>(xr, px, idx);
+            const V zi = CPLX ? vload<P>(xi, px, idx) : vzero<P>();
+            FastEngine<P> g;
+            estrin_point<P, CPLX>(n, coef + off, pc, zr, zi, hr, hi, g);
+            if (g.failed()) {
+                NativeEngine<typename P::T> nat;
+                estrin_point<P, CPLX>(n, coef + off, pc, zr, zi, hr, hi, nat);
+            }
+        }
+        vstore<P>(yr, py, idx, hr);
+        if (CPLX) vstore<P>(yi, py, idx, hi);
+    }
+}
+
+template <class P>
+static mp_status polyeval_estrin_launch(int64_t npoly, const int64_t *coef_off, const typename P::T *coef,
+                                        int64_t pc, int64_t npts, const typename P::T *xr, const typename P::T *xi,
+                                        int64_t px, typename P::T *yr, typename P::T *yi, int64_t py, mp_stream s)
+{
+    if (npoly < 0 || npts < 0) return MP_EINVAL;
+    const int64_t total = npoly * npts;
+    if (total == 0) return MP_OK;
+    if (coef_off == nullptr || coef == nullptr || pc < 1 || !planes_ok(xr, total, px) ||
+        !planes_ok(yr, total, py))
+        return MP_EINVAL;
+    if ((xi == nullptr) != (yi == nullptr)) return MP_EINVAL;
+    const unsigned gsz = grid_for(total, 256, 8);
+    if (xi)
+        k_polyeval_estrin<P, true><<<gsz, 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, xr, xi, px, yr,
+                                                                   yi, py);
+    else
+        k_polyeval_estrin<P, false><<<gsz, 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, xr, xi, px, yr,
+                                                                    yi, py);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------
 
@@ -404,6 +561,14 @@ extern "C" {
     {                                                                                               \
         return polyeval_launch<PT>(npoly, coef_off, coef, pcoef, npts, x_re, x_im, px, y_re, y_im, \
                                    py, s);                                                          \
+    }                                                                                               \
+    mp_status mp_polyeval_estrin_##S(int64_t npoly, const int64_t *coef_off, const PT::T *coef,    \
+                                     int64_t pcoef, int64_t npts, const PT::T *x_re,                \
+                                     const PT::T *x_im, int64_t px, PT::T *y_re, PT::T *y_im,       \
+                                     int64_t py, mp_stream s)                                       \
+    {                                                                                               \
+        return polyeval_estrin_launch<PT>(npoly, coef_off, coef, pcoef, npts, x_re, x_im, px, y_re, \
+                                          y_im, py, s);                                             \
     }                                                                                               \
     size_t mp_polyeval_backward_workspace_##S(int64_t npoly, int64_t npts)                          \
     {                                                                                               \

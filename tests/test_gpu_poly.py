@@ -37,6 +37,30 @@ def test_polyeval_bit_exact(mp, oracle, prec):
     assert same_bits(host(yr), wr) and same_bits(host(yi), wi)
 
 
+@pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd", "ds", "tf", "qf"])
+def test_polyeval_estrin_bit_exact(mp, oracle, prec):
+    """Estrin's scheme: the GPU's streamed binary-counter form against the oracle's
+    level-by-level tree, ragged degrees 0..300 (every pass-through pattern up to
+    nine levels), real and complex arguments."""
+    K, dt = oracle.PRECS[prec]
+    off, coef = ragged(31, 12, 0, 300, K, dt)
+    off[3] = off[2]  # an empty polynomial
+    npts = 9
+    npoly = len(off) - 1
+    xr = inputs.mp_uniform(32, npoly * npts, K, dt, stream=inputs.STREAM_X)
+    xi = inputs.mp_uniform(33, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    doff, dcoef = dev(off), dev(coef)
+    y = mp.polyeval(prec, doff, dcoef, npts, dev(xr), scheme="estrin")
+    assert same_bits(host(y), oracle.polyeval_estrin(prec, off, coef, npts, xr))
+    yr, yi = mp.polyeval(prec, doff, dcoef, npts, dev(xr), dev(xi), scheme="estrin")
+    wr, wi = oracle.polyeval_estrin(prec, off, coef, npts, xr, xi)
+    assert same_bits(host(yr), wr) and same_bits(host(yi), wi)
+    if dt == np.float64:  # points near 2^-1000: the per-point FP64 recomputation
+        xr[:, 0::5] *= 2.0 ** -1000
+        y = mp.polyeval(prec, doff, dcoef, npts, dev(xr), scheme="estrin")
+        assert same_bits(host(y), oracle.polyeval_estrin(prec, off, coef, npts, xr))
+
+
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
 @pytest.mark.parametrize("npts", [0, 1, 77])
 @pytest.mark.parametrize("dmax", [70, 200])
