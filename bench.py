@@ -435,11 +435,14 @@ def extras(prec="qd", quick=False):
     return out
 
 
-def dk_instr(prec, degrees, iters):
+def dk_instr(prec, degrees, iters, hybrid=False):
     """FP64 instructions of the Durand-Kerner sweeps: per root and sweep, n complex
-    Horner steps (4 mul + 3 add) and n - 1 product steps (2 sub + 4 mul + 2 add)."""
+    Horner steps (4 mul + 3 add) and n - 1 product steps (2 sub + 4 mul + 2 add).
+    hybrid=True counts what the hybrid engine issues (TwoSum's error terms on the
+    integer pipes), else the paper's all-FP64 sequence."""
     d = degrees.astype(np.float64)
-    per_root = d * (4 * INSTR_MUL[prec] + 3 * INSTR_ADD[prec]) + (d - 1) * (4 * INSTR_MUL[prec] + 4 * INSTR_ADD[prec])
+    mu, ad = mul_instr(prec, hybrid), add_instr(prec, hybrid)
+    per_root = d * (4 * mu + 3 * ad) + (d - 1) * (4 * mu + 4 * ad)
     return float(np.sum(iters.astype(np.float64) * d * per_root))
 
 
@@ -468,20 +471,23 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
     torch.cuda.synchronize()
     tb = e0.elapsed_time(e1) / 1e3
     it, st, r = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
-    instr = dk_instr(prec, prob.degrees, it)
+    instr = dk_instr(prec, prob.degrees, it, hybrid=True)
+    instr_paper = dk_instr(prec, prob.degrees, it)
     peak = NOMINAL_FP64_TFLOPS * 1e12 / 2
     res = {"polys": npoly, "degrees": "uniform [10, 500]", "sweeps_cap": sweeps, "batched_graph_s": tb,
+           "engine": "hybrid (default)",
            "root_sweeps_per_s": float(np.sum(prob.degrees * it)) / tb,
            "fp64_instr_per_s": instr / tb, "fp64_instr_frac": instr / tb / peak,
+           "paper_sequence_equiv_frac": instr_paper / tb / peak,
            "status_counts": np.bincount(st, minlength=5).tolist()}
-    # the same replay with the hybrid engine (opts.engine = 1): same bits, time for comparison
-    gh = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=sweeps, sort=1, engine=1)
+    # the same replay with every step on the FP64 pipe (opts.engine = 2): same bits
+    gh = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=sweeps, sort=1, engine=2)
     e0.record()
     rh, ith, _ = gh.replay()
     e1.record()
     torch.cuda.synchronize()
-    res["hybrid_engine_graph_s"] = e0.elapsed_time(e1) / 1e3
-    res["hybrid_engine_identical_bits"] = bool(torch.equal(rh.view(torch.int64), g.roots.view(torch.int64)) and
+    res["fp64_engine_graph_s"] = e0.elapsed_time(e1) / 1e3
+    res["fp64_engine_identical_bits"] = bool(torch.equal(rh.view(torch.int64), g.roots.view(torch.int64)) and
                                                np.array_equal(ith.cpu().numpy(), it))
     del gh
     order = np.argsort(prob.degrees, kind="stable")
@@ -503,7 +509,7 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
     same = all(np.array_equal(rl[:, so[q] - q:so[q + 1] - q - 1].view(np.uint64),
                               np.ascontiguousarray(r[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
                for q, b in enumerate(sel))
-    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy())
+    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy(), hybrid=True)
     res["per_poly_loop_sample"] = {
         "polys": len(sel), "degrees": prob.degrees[sel].tolist(), "loop_s": tl,
         "fp64_instr_per_s": instr_l / tl, "identical_bits_to_batched": bool(same),
@@ -512,7 +518,7 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
     return res
 
 
-def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None):
+def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None, engine=0):
     """The paper's Durand-Kerner problem (Section 4.2, Eq. 6, n = 64; Table 6): one solve
     on the GPU (latency), a batch of `copies` identical problems in one persistent
     launch (throughput), and the oracle's single solve on one host core."""
@@ -545,10 +551,28 @@ def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None):
     res = {"n": n, "precision": prec, "sweeps": int(it.cpu()[0]), "status": int(st.cpu()[0]),
            "single_solve_gpu_s": t1, "batch_copies": copies, "batch_s": tb,
            "batch_solves_per_s": copies / tb,
-           "batch_fp64_instr_frac": dk_instr(prec, np.full(copies, n), itb.cpu().numpy()) / tb /
-           (NOMINAL_FP64_TFLOPS * 1e12 / 2),
+           "batch_fp64_instr_frac": dk_instr(prec, np.full(copies, n), itb.cpu().numpy(), hybrid=engine != 2) /
+           tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
            "paper_table6_s": {"EPYC BF AVX2": 0.415, "EPYC BF": 0.628, "Snapdragon BF Neon": 0.336,
                               "Snapdragon BF": 0.383}}
+    # the other engine on the same problems (same bits)
+    other = 2 if engine != 2 else 1
+    mpg.roots(prec, off1, c1, n, engine=other)
+    torch.cuda.synchronize()
+    e0.record()
+    r2, _, _ = mpg.roots(prec, off1, c1, n, engine=other)
+    e1.record()
+    torch.cuda.synchronize()
+    t2 = e0.elapsed_time(e1) / 1e3
+    g2 = mpg.RootsGraph(prec, offb, cb, n, engine=other)
+    e0.record()
+    rb2, _, _ = g2.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    res["other_engine"] = {"engine": "FP64 pipe" if other == 2 else "hybrid", "single_solve_gpu_s": t2,
+                           "batch_s": e0.elapsed_time(e1) / 1e3,
+                           "identical_bits": bool(torch.equal(r2.view(torch.int64), r.view(torch.int64)) and
+                                                  torch.equal(rb2.view(torch.int64), rb.view(torch.int64)))}
     if pool is not None:
         res["oracle_single_core_s"] = pool.pool.apply(_oracle_chebyshev, ((prec, n),))
     return res
@@ -588,7 +612,7 @@ def roots_workload(a):
                                int(prob.coef_off[-1]))
     off = dev(prob.coef_off)
     # constructing the graph runs the solve once outside capture: that run is the warm-up
-    g = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=a.max_iter, sort=1)
+    g = mpg.RootsGraph(prec, off, coef, maxdeg, radius=1.1, max_iter=a.max_iter, sort=1, engine=a.dk_engine)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record()
@@ -597,7 +621,9 @@ def roots_workload(a):
         torch.cuda.synchronize()
     tb = e0.elapsed_time(e1) / 1e3
     it, st, r = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
-    instr = dk_instr(prec, prob.degrees, it)
+    hyb = a.dk_engine != 2
+    instr = dk_instr(prec, prob.degrees, it, hybrid=hyb)
+    instr_paper = dk_instr(prec, prob.degrees, it)
     order = np.argsort(prob.degrees, kind="stable")
     sel = order[np.linspace(0, a.npoly - 1, a.loop_polys).astype(int)]
     hc = coef.cpu().numpy()
@@ -606,7 +632,8 @@ def roots_workload(a):
     sc = np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in sel], 1)
     md = int(prob.degrees[sel].max())
     e0.record()
-    rl, itl, stl = mpg.roots(prec, dev(so), dev(sc), md, radius=1.1, max_iter=a.max_iter, mode=1)
+    rl, itl, stl = mpg.roots(prec, dev(so), dev(sc), md, radius=1.1, max_iter=a.max_iter, mode=1,
+                             engine=a.dk_engine)
     e1.record()
     torch.cuda.synchronize()
     tl = e0.elapsed_time(e1) / 1e3
@@ -614,17 +641,19 @@ def roots_workload(a):
     same = all(np.array_equal(rl[:, so[q] - q:so[q + 1] - q - 1].view(np.uint64),
                               np.ascontiguousarray(r[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
                for q, b in enumerate(sel))
-    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy())
+    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy(), hybrid=hyb)
     roots_total = int(prob.degrees.sum())
     out = {"metric": "batched roots/s", "value": roots_total / tb, "unit": "roots/s",
            "higher_is_better": True, "n_gpus": 1, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"{a.npoly} {prec.upper()} polynomials, degrees uniform [10, 500], roots "
                                   "in the unit disk, 1e-30 perturbation, start radius 1.1, "
-                                  f"<= {a.max_iter} sweeps; one CUDA-graph replay"},
+                                  f"<= {a.max_iter} sweeps; one CUDA-graph replay",
+                      "engine": "FP64 pipe" if a.dk_engine == 2 else "hybrid (TwoSum error terms on the integer pipes)"},
            "batched_s": tb, "roots": roots_total, "sweeps_mean": float(it.mean()), "sweeps_max": int(it.max()),
            "status_counts": {"cap": int(np.sum(st == 0)), "converged": int(np.sum(st == 1)),
                              "stagnated": int(np.sum(st == 2)), "breakdown": int(np.sum(st == 4))},
            "fp64_instr_per_s": instr / tb, "fp64_instr_frac": instr / tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
+           "paper_sequence_equiv_frac": instr_paper / tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
            "per_poly_loop_sample": {"polys": len(sel), "degrees": prob.degrees[sel].tolist(),
                                     "sweeps": itl.cpu().numpy().tolist(), "loop_s": tl,
                                     "identical_bits_to_batched": bool(same),
@@ -679,7 +708,7 @@ def profile_one(a):
         md = int(prob.degrees.max())
         coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), md,
                                    int(prob.coef_off[-1]))
-        mpg.roots(prec, dev(prob.coef_off), coef, md, radius=1.1, max_iter=2, sort=1)
+        mpg.roots(prec, dev(prob.coef_off), coef, md, radius=1.1, max_iter=2, sort=1, engine=a.dk_engine)
     torch.cuda.synchronize()
     print("ok", a.profile, a.n)
 
@@ -818,6 +847,9 @@ def main(argv=None):
     ap.add_argument("--npoly", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--loop-polys", type=int, default=8)
+    ap.add_argument("--dk-engine", type=int, default=0, choices=[0, 1, 2],
+                    help="Durand-Kerner engine for --workload roots and --profile dk: 0 automatic (hybrid), "
+                         "1 hybrid, 2 FP64 pipe")
     ap.add_argument("--profile", choices=["gemm", "horner", "dcoef", "dk", "peak"], default=None,
                     help="run one launch of this kernel family at size --n (for ncu) and exit")
     a = ap.parse_args(argv)

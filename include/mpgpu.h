@@ -284,12 +284,11 @@ mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off
 /* a clock64 budget per polynomial) stopped it.  Results, iteration counts  */
 /* and statuses are bit-identical to the CPU oracle and identical between   */
 /* the persistent batched launch (mode 0) and one launch per polynomial     */
-/* (mode 1), and between the two engines: engine 1 runs each root's update  */
-/* on the hybrid engine (TwoSum error terms on the integer pipes, see GEMM; */
-/* a root whose integer path leaves its domain is recomputed on the FP64    */
-/* pipe).  The default (0) keeps everything on the FP64 pipe: the update's  */
-/* dependency chains leave too little parallelism for the hybrid engine to  */
-/* pay at the batched workload's sizes.                                      */
+/* (mode 1), and between the engines: the hybrid engine (opts->engine 0 =   */
+/* automatic, or 1) runs each root's update with TwoSum error terms on the  */
+/* integer pipes (see GEMM), the multicomponent add and multiply called out */
+/* of line; a root whose integer path leaves its domain is recomputed on the*/
+/* FP64 pipe.  opts->engine 2 keeps every step on the FP64 pipe.            */
 /*   roots  : complex K-array, root j of polynomial b at index              */
 /*            coef_off[b] - b + j, plane stride proots                       */
 /*   z0     : NULL or starting values in the same layout (plane stride pz0)  */
@@ -308,10 +307,10 @@ typedef struct {
     double radius;           /* > 0: start circle radius instead of Eq. 5's */
     int64_t watchdog_cycles; /* > 0: per-polynomial clock64 budget, status 3 when spent */
     int32_t max_degree;      /* host bound on every degree, required */
-    int32_t threads;         /* threads per block: 0 = 128 (engine 0) or 256 (engine 1); else a multiple of 32, <= 256 */
+    int32_t threads;         /* threads per block: 0 = 256 (hybrid) or 128 (engine 2); else a multiple of 32, <= 256 */
     int32_t blocks_per_sm;   /* persistent grid = SMs * blocks_per_sm, 0 = automatic */
     int32_t sort;            /* 1: process polynomials in descending degree (default 0 = off) */
-    int32_t engine;          /* 0: FP64 pipe throughout (default); 1: hybrid engine; same bits */
+    int32_t engine;          /* 0: automatic (hybrid), 1: hybrid, 2: FP64 pipe throughout; same bits */
 } mp_roots_opts;
 
 #define MPGPU_DECL_ROOTS(P)                                                                 \

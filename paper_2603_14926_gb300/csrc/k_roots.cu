@@ -219,6 +219,59 @@ __device__ void block_max2(DKShared &sh, double a, double b, int bad)
     __syncthreads();
 }
 
+// The hybrid engine's multicomponent add and multiply, called out of line.  The
+// root update holds about fifteen of them per step; inlined, the hybrid code
+// overflows the instruction cache.  Each call runs its own engine and hands its
+// domain flag back with the result.
+template <class P> struct HybridResult {
+    typename P::V v;
+    uint32_t bad;
+};
+
+template <class P>
+__device__ __noinline__ HybridResult<P> hybrid_add_call(typename P::V a, typename P::V b)
+{
+    HybridEngine<false> h;
+    const typename P::V r = P::add(a, b, h);
+    return {r, h.bad};
+}
+
+template <class P>
+__device__ __noinline__ HybridResult<P> hybrid_mul_call(typename P::V a, typename P::V b)
+{
+    HybridEngine<false> h;
+    const typename P::V r = P::mul(a, b, h);
+    return {r, h.bad};
+}
+
+// A precision tag whose add and multiply on the hybrid engine are those calls
+// (the native engine stays inline).
+template <class P> struct OutlinedHybrid : P {
+    using V = typename P::V;
+    static __device__ __forceinline__ V add(const V &a, const V &b, HybridEngine<false> &g)
+    {
+        const HybridResult<P> r = hybrid_add_call<P>(a, b);
+        g.bad |= r.bad;
+        return r.v;
+    }
+    static __device__ __forceinline__ V mul(const V &a, const V &b, HybridEngine<false> &g)
+    {
+        const HybridResult<P> r = hybrid_mul_call<P>(a, b);
+        g.bad |= r.bad;
+        return r.v;
+    }
+    template <class E> static __device__ __forceinline__ V add(const V &a, const V &b, E &g)
+    {
+        return P::add(a, b, g);
+    }
+    template <class E> static __device__ __forceinline__ V mul(const V &a, const V &b, E &g)
+    {
+        return P::mul(a, b, g);
+    }
+    static __device__ __forceinline__ V add(const V &a, const V &b) { return P::add(a, b); }
+    static __device__ __forceinline__ V mul(const V &a, const V &b) { return P::mul(a, b); }
+};
+
 // One root's Durand-Kerner update (Eq. 4): w_i = q(z_i) / prod_{j != i} (z_i - z_j)
 // with extended exponents for both factors, y_i = z_i - w_i; every multicomponent
 // operation on the engine g.
@@ -230,45 +283,47 @@ __device__ __forceinline__ void dk_update(int64_t i, int64_t n, const double *c,
 {
     using V = typename P::V;
     constexpr int K = P::K;
-    // q(z_i) with extended exponent
+    // q(z_i) (Horner, coefficients n-1 down to 0) and prod_{j != i} (z_i - z_j)
+    // (j ascending) are independent recurrences: one loop advances both, so the
+    // two dependency chains overlap; each keeps its own order and exponent.
     V hr = vload<P>(c, cap, n), hi = vzero<P>();
     long long Eq = 0;
-    for (int64_t kk = n - 1; kk >= 0; kk--) {
-        V a = vload<P>(c, cap, kk);
-        if (Eq > 1000) a = vzero<P>();
-        else if (Eq > 0) vscale<P>(a, (int)-Eq);
-        V t1 = P::mul(hr, zr, g);
-        V t2 = P::mul(hi, zi, g);
-        t1 = vsub<P>(t1, t2, g);
-        t1 = P::add(t1, a, g);
-        V t3 = P::mul(hr, zi, g);
-        V t4 = P::mul(hi, zr, g);
-        hi = P::add(t3, t4, g);
-        hr = t1;
-        const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
-        if (be >= 1023 + DK_RESCALE + 1) {
-            vscale<P>(hr, -DK_RESCALE);
-            vscale<P>(hi, -DK_RESCALE);
-            Eq += DK_RESCALE;
-        }
-    }
-    // prod_{j != i} (z_i - z_j) with extended exponent
     V dr = vone<P>(), di = vzero<P>();
     long long Ed = 0;
-    for (int64_t j = 0; j < n; j++) {
-        if (j == i) continue;
-        const V tr = vsub<P>(zr, vload<P>(z, zc, j), g);
-        const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, j), g);
-        cmul<P>(dr, di, tr, ti, dr, di, g);
-        const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
-        if (be >= 1023 + DK_RESCALE + 1) {
-            vscale<P>(dr, -DK_RESCALE);
-            vscale<P>(di, -DK_RESCALE);
-            Ed += DK_RESCALE;
-        } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
-            vscale<P>(dr, DK_RESCALE);
-            vscale<P>(di, DK_RESCALE);
-            Ed -= DK_RESCALE;
+    for (int64_t t = 0; t < n; t++) {
+        {  // Horner step on coefficient n-1-t
+            V a = vload<P>(c, cap, n - 1 - t);
+            if (Eq > 1000) a = vzero<P>();
+            else if (Eq > 0) vscale<P>(a, (int)-Eq);
+            V t1 = P::mul(hr, zr, g);
+            V t2 = P::mul(hi, zi, g);
+            t1 = vsub<P>(t1, t2, g);
+            t1 = P::add(t1, a, g);
+            V t3 = P::mul(hr, zi, g);
+            V t4 = P::mul(hi, zr, g);
+            hi = P::add(t3, t4, g);
+            hr = t1;
+            const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+            if (be >= 1023 + DK_RESCALE + 1) {
+                vscale<P>(hr, -DK_RESCALE);
+                vscale<P>(hi, -DK_RESCALE);
+                Eq += DK_RESCALE;
+            }
+        }
+        if (t != i) {  // product step with j = t
+            const V tr = vsub<P>(zr, vload<P>(z, zc, t), g);
+            const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, t), g);
+            cmul<P>(dr, di, tr, ti, dr, di, g);
+            const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
+            if (be >= 1023 + DK_RESCALE + 1) {
+                vscale<P>(dr, -DK_RESCALE);
+                vscale<P>(di, -DK_RESCALE);
+                Ed += DK_RESCALE;
+            } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
+                vscale<P>(dr, DK_RESCALE);
+                vscale<P>(di, DK_RESCALE);
+                Ed -= DK_RESCALE;
+            }
         }
     }
     cdiv<P>(hr, hi, dr, di, wr, wi, g);
@@ -384,7 +439,8 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
             const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
             V yr, yi, wr, wi;
             E g;
-            dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
+            using PU = typename std::conditional<std::is_same<E, HybridEngine<false>>::value, OutlinedHybrid<P>, P>::type;
+            dk_update<PU>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
             if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
             vstore<P>(zn, pn, i, yr);
             vstore<P>(zn + K * pn, pn, i, yi);
@@ -569,10 +625,11 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         return MP_EINVAL;
     if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
     if (o->mode != 0 && o->mode != 1) return MP_EINVAL;
-    if (o->engine != 0 && o->engine != 1) return MP_EINVAL;
+    if (o->engine < 0 || o->engine > 2) return MP_EINVAL;
+    const bool hybrid = o->engine != 2;  // 0 = automatic: the hybrid engine
     const int threads = o->threads > 0 ? o->threads
-                                       : (o->engine == 1 ? DKLaunch<HybridEngine<false>>::default_threads
-                                                         : DKLaunch<NativeEngine<double>>::default_threads);
+                                       : (hybrid ? DKLaunch<HybridEngine<false>>::default_threads
+                                                 : DKLaunch<NativeEngine<double>>::default_threads);
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
     if (ws == nullptr) return MP_EINVAL;
@@ -606,8 +663,8 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         if (e != MP_OK) return e;
         A.order = order;
     }
-    return o->engine == 1 ? dk_run<P, HybridEngine<false>>(A, o, npoly, threads, smem, st)
-                          : dk_run<P, NativeEngine<double>>(A, o, npoly, threads, smem, st);
+    return hybrid ? dk_run<P, HybridEngine<false>>(A, o, npoly, threads, smem, st)
+                  : dk_run<P, NativeEngine<double>>(A, o, npoly, threads, smem, st);
 }
 
 template <class P>

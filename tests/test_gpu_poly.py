@@ -148,7 +148,7 @@ def _solve_both(mp, oracle, prec, prob, coef, **kw):
 
 
 @pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
-@pytest.mark.parametrize("engine", [0, 1])
+@pytest.mark.parametrize("engine", [0, 2])
 def test_roots_bit_exact(mp, oracle, prec, engine):
     prob = inputs.dk_problem(3, 6, 10, 40)
     coef = oracle.poly_from_roots(prec, prob)
@@ -160,7 +160,7 @@ def test_roots_bit_exact(mp, oracle, prec, engine):
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd"])
 def test_roots_range_limits_bit_exact(mp, oracle, prec):
-    """Hybrid engine (opts.engine = 1).  One starting value per polynomial placed
+    """Hybrid engine (the default).  One starting value per polynomial placed
     near 2^-1000 makes the first sweep's Horner products leave the hybrid engine's
     domain (subnormal error terms): that root is recomputed on the FP64 pipe, and roots, sweep counts and
     statuses stay bit-identical to the oracle.  (Two such starting values would
@@ -182,8 +182,8 @@ def test_roots_range_limits_bit_exact(mp, oracle, prec):
     assert same_bits(np.ascontiguousarray(host(r)), wr)
 
 
-@pytest.mark.parametrize("mode,sort,threads,engine", [(0, 0, 64, 0), (0, 1, 256, 0), (1, 0, 128, 0), (1, 1, 32, 0),
-                                                      (0, 1, 256, 1), (1, 0, 64, 1)])
+@pytest.mark.parametrize("mode,sort,threads,engine", [(0, 0, 64, 2), (0, 1, 256, 2), (1, 0, 128, 2), (1, 1, 32, 2),
+                                                      (0, 1, 256, 1), (1, 0, 64, 1), (0, 0, 128, 0)])
 def test_roots_modes_identical(mp, oracle, mode, sort, threads, engine):
     """Persistent batched launch and the per-polynomial launch loop, sorted or not,
     any block size: identical bits, equal to the oracle."""
