@@ -420,7 +420,8 @@ template <class P> struct GemmTable<P, true> {
     using N = NativeEngine<double>;
     using H = HybridEngine<false>;
     using HQ = HybridEngine<true>;
-    static constexpr int count = 9;
+    using HP = HybridEngine<false, true>;
+    static constexpr int count = 10;
     static const char *name(int c)
     {
         switch (c) {
@@ -433,6 +434,7 @@ template <class P> struct GemmTable<P, true> {
         case 6: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum + QuickTwoSum";
         case 7: return "BM32 BN32 BK16 TM2 TN2 (256 thr), hybrid TwoSum";
         case 8: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum, 1 block/SM register budget";
+        case 9: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum + TwoProd";
         }
         return nullptr;
     }
@@ -448,6 +450,7 @@ template <class P> struct GemmTable<P, true> {
         case 6: return gemm_run_tma<P, HQ, 2, 32, 32, 16, 2, 2>(a...);
         case 7: return gemm_run<P, H, 2, 32, 32, 16, 2, 2>(a...);
         case 8: return gemm_run_tma<P, H, 1, 32, 32, 16, 2, 2>(a...);
+        case 9: return gemm_run_tma<P, HP, 2, 32, 32, 16, 2, 2>(a...);
         default: return gemm_run<P, N, 2, 32, 32, 16, 2, 2>(a...);
         }
     }

@@ -82,8 +82,10 @@ __device__ __forceinline__ void two_prod(T a, T b, T &p, T &e)
 // NativeEngine<T>: every step on the FP64 (or FP32) pipe, as printed.
 // HybridEngine<QTS>: binary64 only.  TwoSum's s from one FP64 add, its error e
 //   from the integer pipes (mp_eft_int.cuh); with QTS also QuickTwoSum's error
-//   where Algorithm 1 is exact (exponent(a) >= exponent(b), or a zero operand).
-//   TwoProd and the plain operations stay on the FP64 pipe.  Outside the
+//   where Algorithm 1 is exact (exponent(a) >= exponent(b), or a zero operand);
+//   with TP also TwoProd's error (p from one FP64 multiply, the error term from
+//   the low 64 bits of the integer significand product).  The plain operations
+//   stay on the FP64 pipe.  Outside the
 //   integer path's domain, and for QuickTwoSum outside its exact case, the
 //   engine raises failed(); callers then recompute the result with
 //   NativeEngine, so every output is the FP64 sequence's bits.
@@ -98,7 +100,7 @@ template <typename T> struct NativeEngine {
     __device__ __forceinline__ bool failed() const { return false; }
 };
 
-template <bool QTS> struct HybridEngine {
+template <bool QTS, bool TP = false> struct HybridEngine {
     uint32_t bad = 0;
     __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
     {
@@ -123,7 +125,18 @@ template <bool QTS> struct HybridEngine {
         e = __longlong_as_double((long long)(Ba == 0 ? B : E));
         s = s_;
     }
-    __device__ __forceinline__ void two_prod(double a, double b, double &p, double &e) { mp::two_prod(a, b, p, e); }
+    __device__ __forceinline__ void two_prod(double a, double b, double &p, double &e)
+    {
+        if (!TP) {
+            mp::two_prod(a, b, p, e);
+            return;
+        }
+        const double p_ = __dmul_rn(a, b);
+        e = __longlong_as_double((long long)eft_int::two_prod_err((uint64_t)__double_as_longlong(a),
+                                                                   (uint64_t)__double_as_longlong(b),
+                                                                   (uint64_t)__double_as_longlong(p_), bad));
+        p = p_;
+    }
     __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     __device__ __forceinline__ bool failed() const { return bad != 0; }

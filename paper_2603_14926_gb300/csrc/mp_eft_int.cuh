@@ -117,5 +117,40 @@ MP_HD uint64_t two_sum_err(uint64_t A, uint64_t B, uint64_t S, uint32_t &bad)
     return mag == 0 ? 0 : mk64(eh, el);
 }
 
+// e = a*b - p for p = fl(a*b) (the error term of Algorithm 3's TwoProd, which
+// FMA(a, b, -p) returns), as a binary64 pattern.  With ma, mb the integer
+// significands and units 2^(Ea+Eb-2150), a*b = ma*mb exactly, and p = mp * 2^sh in
+// those units with sh = Ep - Ea - Eb + 1075 in {52, 53, 54} for normal operands;
+// |e| <= ulp(p)/2 < 2^54 units, so e = ma*mb - mp*2^sh evaluated modulo 2^64 (the
+// low 64 bits of the 106-bit product, three multiplications on the FMA pipe) is
+// exact as a signed value; its sign is then applied relative to p's.  Domain:
+// a and b normal with p normal, or a zero operand (e = +0); e zero or normal;
+// elsewhere `bad` is raised.
+MP_HD uint64_t two_prod_err(uint64_t A, uint64_t B, uint64_t P, uint32_t &bad)
+{
+    int ea, eb, ep;
+    uint64_t ma, mb, mp;
+    unpack(A, ea, ma);
+    unpack(B, eb, mb);
+    unpack(P, ep, mp);
+    const uint64_t lo = ma * mb;                                      // low 64 bits of the product
+    const int sh = ep - ea - eb + 1075;
+    const uint64_t ei = lo - shl_mod(mp, (uint32_t)sh);
+    const uint64_t kn = (uint64_t)((int64_t)ei >> 63);
+    const uint64_t mag = (ei ^ kn) - kn;
+    const int lz = clz64(mag);
+    const uint64_t norm = shl_mod(mag, (uint32_t)lz & 63u);
+    const int be = ea + eb - 1064 - lz;                              // biased exponent of e
+    const uint32_t sign = (hi32(A) ^ hi32(B) ^ hi32(kn)) & 0x80000000u;
+    const uint32_t eh = ((hi32(norm) >> 11) + ((uint32_t)(be - 1) << 20)) | sign;
+    const uint32_t el = shr11_lo(lo32(norm), hi32(norm));
+    const uint32_t Ea = (hi32(A) >> 20) & 0x7FFu, Eb = (hi32(B) >> 20) & 0x7FFu, Ep = (hi32(P) >> 20) & 0x7FFu;
+    const bool za = ((A << 1) == 0), zb = ((B << 1) == 0), zp = ((P << 1) == 0);
+    bad |= (uint32_t)(Ea == 0 && !za && !zb) | (uint32_t)(Eb == 0 && !zb && !za) | (uint32_t)(Ea == 0x7FF) |
+           (uint32_t)(Eb == 0x7FF) | (uint32_t)(Ep == 0x7FF) | (uint32_t)(Ep == 0 && !zp) |
+           (uint32_t)(mag != 0 && be < 1) | (uint32_t)(!za && !zb && (sh < 52 || sh > 54));
+    return mag == 0 ? 0 : mk64(eh, el);
+}
+
 }  // namespace eft_int
 }  // namespace mp

@@ -40,6 +40,29 @@ static double random_frac_double(int emin, int emax)
 }
 
 static long checked = 0, accepted = 0, wrong = 0, refused_in_domain = 0;
+static long pchecked = 0, paccepted = 0, pwrong = 0, prefused = 0;
+
+// TwoProd error term against the host's correctly rounded fma
+static void check_prod(double a, double b, bool in_domain)
+{
+    volatile double p = a * b;
+    const double e = std::fma(a, b, -p);
+    uint32_t bad = 0;
+    const uint64_t got = mp::eft_int::two_prod_err(bits(a), bits(b), bits(p), bad);
+    pchecked++;
+    if (bad) {
+        if (in_domain) {
+            if (prefused < 5) std::printf("product refused in domain: a=%a b=%a\n", a, b);
+            prefused++;
+        }
+        return;
+    }
+    paccepted++;
+    if (got != bits(e)) {
+        if (pwrong < 10) std::printf("product wrong: a=%a b=%a  got %a  want %a\n", a, b, dbl(got), e);
+        pwrong++;
+    }
+}
 
 static void check(double a, double b, bool in_domain)
 {
@@ -73,7 +96,10 @@ int main(int argc, char **argv)
                               0x1.fffffffffffffp+1023, -0x1.fffffffffffffp+1022, 0x1p+1023, INFINITY, -INFINITY,
                               NAN, 0x1p-960, 0x1.0000000000001p-960};
     for (double a : special)
-        for (double b : special) check(a, b, false);
+        for (double b : special) {
+            check(a, b, false);
+            check_prod(a, b, false);
+        }
     for (long i = 0; i < pairs; i++) {
         const int mode = (int)(next() % 10);
         double a = random_frac_double(64, 2045), b;
@@ -107,7 +133,29 @@ int main(int argc, char **argv)
             if (e != 0 && std::fabs(e) < 0x1p-1022) dom = false;
         }
         check(a, b, dom);
+        // products: exponents spread around the range, ties and zeros included
+        {
+            double c = random_frac_double(1, 2046), d;
+            const int ec = (int)((bits(c) >> 52) & 0x7FF);
+            int ed = 2046 - ec + (int)(next() % 1200) - 600;  // product exponent around the middle of the range
+            if (ed < 1) ed = 1;
+            if (ed > 2046) ed = 2046;
+            d = make(ed, next() & ((1ull << 52) - 1), next() & 1);
+            if (next() % 8 == 0) d = dbl(bits(d) & ~((1ull << (next() % 53)) - 1));
+            if (next() % 16 == 0) d = (next() & 1) ? -0.0 : 0.0;
+            if (next() % 32 == 0) c = random_frac_double(0, 3);  // subnormal and tiny operands
+            volatile double p = c * d;
+            const double e = std::fma(c, d, -p);
+            const int pc = (int)((bits(c) >> 52) & 0x7FF), pd = (int)((bits(d) >> 52) & 0x7FF);
+            // domain: both operands normal with a finite normal product whose unit 2^(Ea+Eb-2150) is
+            // normal (so any nonzero error is normal too), or a zero operand
+            const bool pdom = (pc >= 1 && pd >= 1 && pc + pd >= 1128 && std::isfinite(p) &&
+                               std::fabs(p) >= 0x1p-1022) || c == 0 || d == 0;
+            check_prod(c, d, pdom);
+        }
     }
     std::printf("checked %ld accepted %ld wrong %ld refused-in-domain %ld\n", checked, accepted, wrong, refused_in_domain);
-    return (wrong || refused_in_domain) ? 1 : 0;
+    std::printf("products: checked %ld accepted %ld wrong %ld refused-in-domain %ld\n", pchecked, paccepted, pwrong,
+                prefused);
+    return (wrong || refused_in_domain || pwrong || prefused) ? 1 : 0;
 }
