@@ -689,11 +689,12 @@ def profile_one(a):
     elif a.profile == "peak":
         names = {0: "DFMA", 1: "DADD", 2: "DMUL", 3: "FFMA", 4: "FADD", 5: "FFMA2 (f32x2, per lane)",
                  6: "FADD2 (f32x2, per lane)", 7: "LOP3 (integer ALU pipe)", 8: "IMAD (integer, FMA pipe)",
-                 9: "IADD3 | LOP3 alternating", 10: "FLO + IADD3 (2 per op)"}
+                 9: "IADD3 | LOP3 alternating", 10: "FLO + IADD3 (2 per op)",
+                 11: "DFMA, one active lane per warp (= warp instructions)"}
         res = {}
         sms = mpg.lib().mp_sm_count()
         for kind, nm in names.items():
-            it = 4096 if kind < 3 else 131072
+            it = 4096 if kind < 3 or kind == 11 else 131072
             best = 0.0
             for per_sm, thr in ((2, 256), (4, 256), (8, 256), (8, 512)):
                 mpg.peak(kind, iters=256, blocks=sms * per_sm, threads=thr)

@@ -359,10 +359,12 @@ MPGPU_DECL_ROOTS(qd)
 /* dependency chains of one instruction kind: 0 = DFMA, 1 = DADD, 2 = DMUL,  */
 /* 3 = FFMA, 4 = FADD, 5 = packed fma.rn.f32x2, 6 = packed add.rn.f32x2,     */
 /* 7 = LOP3 (integer ALU pipe), 8 = IMAD (integer on the FMA pipe),          */
-/* 9 = IADD3 and LOP3 alternating, 10 = FLO + IADD3 (count leading zeros).   */
+/* 9 = IADD3 and LOP3 alternating, 10 = FLO + IADD3 (count leading zeros),   */
+/* 11 = DFMA with one active lane per warp.                                   */
 /* SYNCHRONIZES the stream; *ms receives the elapsed time between CUDA      */
 /* events recorded on it and *lane_ops the number of per-lane operations     */
-/* executed (blocks * threads * iters * 8, doubled for kinds 5, 6 and 10).  */
+/* executed (blocks * threads * iters * 8, doubled for kinds 5, 6 and 10;    */
+/* for kind 11 one lane per warp).                                           */
 /* ------------------------------------------------------------------------ */
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms,
                       double *lane_ops, mp_stream stream);

@@ -317,7 +317,19 @@ __device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsign
 template <int KIND>
 __global__ void k_peak(int64_t iters, double *sink)
 {
-    if (KIND >= 7) {  // integer pipes; inline PTX so the chains cannot be folded
+    if (KIND == 11) {  // DFMA with one active lane per warp: the FP64 pipe's cost per warp instruction
+        if ((threadIdx.x & 31) != 0) return;
+        double a[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] = 1.0 + 1e-9 * (threadIdx.x + 8 * j);
+        for (int64_t it = 0; it < iters; it++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) a[j] = __fma_rn(a[j], 0.999999999, 1e-12);
+        double s = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) s += a[j];
+        if (s == 1234.5) sink[0] = s;
+    } else if (KIND >= 7) {  // integer pipes; inline PTX so the chains cannot be folded
         unsigned a[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) a[j] = threadIdx.x * 7u + (unsigned)j;
@@ -415,7 +427,7 @@ int mp_sm_count(void) { return sm_count(); }
 mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *ms, double *lane_ops,
                       mp_stream stream)
 {
-    if (kind < 0 || kind > 10 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
+    if (kind < 0 || kind > 11 || iters <= 0 || blocks <= 0 || threads <= 0 || threads > 1024 ||
         ms == nullptr || lane_ops == nullptr)
         return MP_EINVAL;
     cudaStream_t s = as_stream(stream);
@@ -439,13 +451,16 @@ mp_status mp_peak_run(int kind, int64_t iters, int blocks, int threads, float *m
     case 7: k_peak<7><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 8: k_peak<8><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     case 9: k_peak<9><<<blocks, threads, 0, s>>>(iters, nullptr); break;
-    default: k_peak<10><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    case 10: k_peak<10><<<blocks, threads, 0, s>>>(iters, nullptr); break;
+    default: k_peak<11><<<blocks, threads, 0, s>>>(iters, nullptr); break;
     }
     st = launch_status();
     cudaEventRecord(e1, s);
     if (st == MP_OK) st = cuda_status(cudaEventSynchronize(e1));
     if (st == MP_OK) st = cuda_status(cudaEventElapsedTime(ms, e0, e1));
-    *lane_ops = (double)blocks * threads * (double)iters * 8.0 * ((kind == 5 || kind == 6 || kind == 10) ? 2.0 : 1.0);
+    *lane_ops = kind == 11 ? (double)blocks * ((threads + 31) / 32) * (double)iters * 8.0
+                           : (double)blocks * threads * (double)iters * 8.0 *
+                                 ((kind == 5 || kind == 6 || kind == 10) ? 2.0 : 1.0);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;

@@ -115,27 +115,29 @@ def roots_key(prec, npoly, max_degree):
 
 
 def best_roots_shape(prec, npoly, max_degree):
+    """Cached (threads, blocks_per_sm, engine) for this bucket, or (0, 0, 0) (built-in)."""
     with _lock:
         e = _load().get(roots_key(prec, npoly, max_degree))
-    return (e["threads"], e["blocks_per_sm"]) if e else (0, 0)
+    return (e["threads"], e["blocks_per_sm"], e.get("engine", 0)) if e else (0, 0, 0)
 
 
 def tune_roots(prec, coef_off, coef, max_degree, sweeps=2, radius=1.1,
-               candidates=((64, 0), (128, 0), (256, 0), (128, 2))):
+               candidates=((128, 0, 2), (256, 0, 1), (128, 0, 1), (64, 0, 1), (128, 2, 1))):
     """Time a few sweeps of the persistent batched solver for each (threads,
-    blocks_per_sm) candidate; cache and return the best and all timings."""
+    blocks_per_sm, engine) candidate (engine 1 hybrid, 2 FP64 pipe; all give the
+    same bits); cache and return the best and all timings."""
     from . import roots
 
     npoly = coef_off.numel() - 1
     times = {}
-    for th, bps in candidates:
-        times[(th, bps)] = _time(lambda th=th, bps=bps: roots(prec, coef_off, coef, max_degree,
-                                                              max_iter=sweeps, radius=radius,
-                                                              threads=th, blocks_per_sm=bps, sort=1), 1)
+    for th, bps, eng in candidates:
+        times[(th, bps, eng)] = _time(lambda th=th, bps=bps, eng=eng: roots(
+            prec, coef_off, coef, max_degree, max_iter=sweeps, radius=radius, threads=th, blocks_per_sm=bps,
+            sort=1, engine=eng), 1)
     best = min(times, key=times.get)
     with _lock:
         _load()[roots_key(prec, npoly, max_degree)] = {
-            "threads": best[0], "blocks_per_sm": best[1],
-            "ms": {f"{a}x{b}": v for (a, b), v in times.items()}}
+            "threads": best[0], "blocks_per_sm": best[1], "engine": best[2],
+            "ms": {f"{a}x{b}e{c}": v for (a, b, c), v in times.items()}}
         _save()
     return best, times

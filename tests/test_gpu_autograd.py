@@ -129,7 +129,7 @@ def test_autotuner_gemm_and_roots(mp, oracle, tmp_path, monkeypatch):
     assert same_bits(host(mp.gemm("dd", dev(A), dev(B))), oracle.gemm("dd", A, B))
     prob = inputs.dk_problem(2, 30, 10, 60)
     coef = dev(oracle.poly_from_roots("dd", prob))
-    (th, bps), t = tune.tune_roots("dd", dev(prob.coef_off), coef, int(prob.degrees.max()))
-    assert th in (64, 128, 256) and (th, bps) in t
-    assert tune.best_roots_shape("dd", 30, int(prob.degrees.max())) == (th, bps)
+    (th, bps, eng), t = tune.tune_roots("dd", dev(prob.coef_off), coef, int(prob.degrees.max()))
+    assert th in (64, 128, 256) and eng in (1, 2) and (th, bps, eng) in t
+    assert tune.best_roots_shape("dd", 30, int(prob.degrees.max())) == (th, bps, eng)
     assert (tmp_path / "tune.json").exists()
