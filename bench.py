@@ -676,7 +676,7 @@ def profile_one(a):
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
     if a.profile == "gemm":
         A, B = make_inputs(prec, a.n, a.seed)
-        mpg.gemm(prec, dev(A), dev(B))
+        mpg.gemm(prec, dev(A), dev(B), config=a.gemm_config)
     elif a.profile in ("horner", "dcoef"):
         npoly, deg, npts = a.n, 256, 4096
         off = torch.arange(0, (npoly + 1) * (deg + 1), deg + 1, dtype=torch.int64, device="cuda")
@@ -848,6 +848,8 @@ def main(argv=None):
     ap.add_argument("--npoly", type=int, default=4096)
     ap.add_argument("--max-iter", type=int, default=1000)
     ap.add_argument("--loop-polys", type=int, default=8)
+    ap.add_argument("--gemm-config", type=int, default=None,
+                    help="GEMM tile/engine configuration for --profile gemm (default: the built-in choice)")
     ap.add_argument("--dk-engine", type=int, default=0, choices=[0, 1, 2],
                     help="Durand-Kerner engine for --workload roots and --profile dk: 0 automatic (hybrid), "
                          "1 hybrid, 2 FP64 pipe")
