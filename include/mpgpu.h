@@ -133,14 +133,15 @@ const char *mp_version(void);
 /* the result is bit-identical to the CPU oracle.  C must not alias A or B. */
 /* mp_gemm_ex_P selects a tile configuration (0 .. mp_gemm_num_configs_P()-1,*/
 /* or -1 for the built-in choice); configurations differ only in speed.     */
-/* Configurations 4, 5, 6 and 8 stage the tiles with TMA (cp.async.bulk.    */
+/* Configurations 4, 5, 6, 8 and 9 stage the tiles with TMA (cp.async.bulk. */
 /* tensor, double buffered on mbarriers) when the operands meet TMA's       */
 /* alignment rules (16-byte aligned base, lda/ldb and plane strides         */
 /* multiples of 16 bytes) and otherwise run the same tile with plain loads. */
-/* For binary64 components configurations 5-8 use the hybrid engine: each   */
+/* For binary64 components configurations 5-9 use the hybrid engine: each   */
 /* TwoSum (Algorithm 2) takes s from the FP64 pipe and its error term from  */
-/* an exact integer computation (and configuration 6 likewise QuickTwoSum   */
-/* where Algorithm 1 is exact).  The bits are the FP64 sequence's; a thread */
+/* an exact integer computation (configuration 6 likewise QuickTwoSum where */
+/* Algorithm 1 is exact, configuration 9 likewise TwoProd's error term,     */
+/* Algorithm 3).  The bits are the FP64 sequence's; a thread                */
 /* whose operands leave the integer path's domain (exponents near the       */
 /* binary64 limits, subnormal error terms, an inexact QuickTwoSum)          */
 /* recomputes its outputs with the FP64 pipe.  The built-in choice (-1) is  */
