@@ -161,11 +161,17 @@ constexpr int DK_RESCALE = 256;
 // Shared-memory layout of one polynomial's solve
 // ---------------------------------------------------------------------------
 
+// Split sweeps (a small polynomial in a wide block): the product chains' exponents
+// and domain flags for the threads that finish the roots.
+constexpr int DK_SPLIT_MAX = 128;
+
 struct DKShared {
     double delta, zmax, center, radius;
     int bad, stop, nnz, pad;
     double red[2][32];
     int redi[32];
+    long long split_e[DK_SPLIT_MAX];
+    int split_bad[DK_SPLIT_MAX];
 };
 
 template <class P> struct DKArgs {
@@ -272,9 +278,74 @@ template <class P> struct OutlinedHybrid : P {
     static __device__ __forceinline__ V mul(const V &a, const V &b) { return P::mul(a, b); }
 };
 
+// One Horner step of q(z_i) on coefficient kk, with the extended exponent Eq.
+template <class P, class E>
+__device__ __forceinline__ void dk_horner_step(const double *c, int64_t cap, int64_t kk, const typename P::V &zr,
+                                               const typename P::V &zi, typename P::V &hr, typename P::V &hi,
+                                               long long &Eq, E &g)
+{
+    using V = typename P::V;
+    V a = vload<P>(c, cap, kk);
+    if (Eq > 1000) a = vzero<P>();
+    else if (Eq > 0) vscale<P>(a, (int)-Eq);
+    V t1 = P::mul(hr, zr, g);
+    V t2 = P::mul(hi, zi, g);
+    t1 = vsub<P>(t1, t2, g);
+    t1 = P::add(t1, a, g);
+    V t3 = P::mul(hr, zi, g);
+    V t4 = P::mul(hi, zr, g);
+    hi = P::add(t3, t4, g);
+    hr = t1;
+    const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(hr, -DK_RESCALE);
+        vscale<P>(hi, -DK_RESCALE);
+        Eq += DK_RESCALE;
+    }
+}
+
+// One step of prod_{j != i} (z_i - z_j) with j given, with the extended exponent Ed.
+template <class P, class E>
+__device__ __forceinline__ void dk_product_step(const double *z, int64_t zc, int64_t j, const typename P::V &zr,
+                                                const typename P::V &zi, typename P::V &dr, typename P::V &di,
+                                                long long &Ed, E &g)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    const V tr = vsub<P>(zr, vload<P>(z, zc, j), g);
+    const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, j), g);
+    cmul<P>(dr, di, tr, ti, dr, di, g);
+    const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(dr, -DK_RESCALE);
+        vscale<P>(di, -DK_RESCALE);
+        Ed += DK_RESCALE;
+    } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
+        vscale<P>(dr, DK_RESCALE);
+        vscale<P>(di, DK_RESCALE);
+        Ed -= DK_RESCALE;
+    }
+}
+
+// w_i = q(z_i) / prod, rescaled by 2^(Eq - Ed), and y_i = z_i - w_i.
+template <class P, class E>
+__device__ __forceinline__ void dk_finish(const typename P::V &hr, const typename P::V &hi, long long Eq,
+                                          const typename P::V &dr, const typename P::V &di, long long Ed,
+                                          const typename P::V &zr, const typename P::V &zi, typename P::V &yr,
+                                          typename P::V &yi, typename P::V &wr, typename P::V &wi, E &g)
+{
+    cdiv<P>(hr, hi, dr, di, wr, wi, g);
+    vscale_big<P>(wr, Eq - Ed);
+    vscale_big<P>(wi, Eq - Ed);
+    yr = vsub<P>(zr, wr, g);
+    yi = vsub<P>(zi, wi, g);
+}
+
 // One root's Durand-Kerner update (Eq. 4): w_i = q(z_i) / prod_{j != i} (z_i - z_j)
 // with extended exponents for both factors, y_i = z_i - w_i; every multicomponent
-// operation on the engine g.
+// operation on the engine g.  q(z_i) (Horner, coefficients n-1 down to 0) and the
+// product (j ascending) are independent recurrences: one loop advances both, so
+// the two dependency chains overlap; each keeps its own order and exponent.
 template <class P, class E>
 __device__ __forceinline__ void dk_update(int64_t i, int64_t n, const double *c, int64_t cap, const double *z,
                                           int64_t zc, const typename P::V &zr, const typename P::V &zi,
@@ -282,55 +353,15 @@ __device__ __forceinline__ void dk_update(int64_t i, int64_t n, const double *c,
                                           typename P::V &wi, E &g)
 {
     using V = typename P::V;
-    constexpr int K = P::K;
-    // q(z_i) (Horner, coefficients n-1 down to 0) and prod_{j != i} (z_i - z_j)
-    // (j ascending) are independent recurrences: one loop advances both, so the
-    // two dependency chains overlap; each keeps its own order and exponent.
     V hr = vload<P>(c, cap, n), hi = vzero<P>();
     long long Eq = 0;
     V dr = vone<P>(), di = vzero<P>();
     long long Ed = 0;
     for (int64_t t = 0; t < n; t++) {
-        {  // Horner step on coefficient n-1-t
-            V a = vload<P>(c, cap, n - 1 - t);
-            if (Eq > 1000) a = vzero<P>();
-            else if (Eq > 0) vscale<P>(a, (int)-Eq);
-            V t1 = P::mul(hr, zr, g);
-            V t2 = P::mul(hi, zi, g);
-            t1 = vsub<P>(t1, t2, g);
-            t1 = P::add(t1, a, g);
-            V t3 = P::mul(hr, zi, g);
-            V t4 = P::mul(hi, zr, g);
-            hi = P::add(t3, t4, g);
-            hr = t1;
-            const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
-            if (be >= 1023 + DK_RESCALE + 1) {
-                vscale<P>(hr, -DK_RESCALE);
-                vscale<P>(hi, -DK_RESCALE);
-                Eq += DK_RESCALE;
-            }
-        }
-        if (t != i) {  // product step with j = t
-            const V tr = vsub<P>(zr, vload<P>(z, zc, t), g);
-            const V ti = vsub<P>(zi, vload<P>(z + K * zc, zc, t), g);
-            cmul<P>(dr, di, tr, ti, dr, di, g);
-            const int be = max(bexp(dr.c[0]), bexp(di.c[0]));
-            if (be >= 1023 + DK_RESCALE + 1) {
-                vscale<P>(dr, -DK_RESCALE);
-                vscale<P>(di, -DK_RESCALE);
-                Ed += DK_RESCALE;
-            } else if (be <= 1023 - DK_RESCALE - 1 && (dr.c[0] != 0.0 || di.c[0] != 0.0)) {
-                vscale<P>(dr, DK_RESCALE);
-                vscale<P>(di, DK_RESCALE);
-                Ed -= DK_RESCALE;
-            }
-        }
+        dk_horner_step<P>(c, cap, n - 1 - t, zr, zi, hr, hi, Eq, g);
+        if (t != i) dk_product_step<P>(z, zc, t, zr, zi, dr, di, Ed, g);
     }
-    cdiv<P>(hr, hi, dr, di, wr, wi, g);
-    vscale_big<P>(wr, Eq - Ed);
-    vscale_big<P>(wi, Eq - Ed);
-    yr = vsub<P>(zr, wr, g);
-    yi = vsub<P>(zi, wi, g);
+    dk_finish<P>(hr, hi, Eq, dr, di, Ed, zr, zi, yr, yi, wr, wi, g);
 }
 
 // The same update on the FP64 pipe, out of line: taken only when the hybrid
@@ -428,6 +459,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     }
     __syncthreads();
 
+    const bool split = nt % 64 == 0 && n <= nt / 2 && n <= DK_SPLIT_MAX;
     const long long t0 = clock64();
     int st = DK_CAP, it = A.max_iter;
     double best = __longlong_as_double(0x7ff0000000000000LL);  // +inf
@@ -435,20 +467,65 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     for (int k = 1; k <= A.max_iter; k++) {
         double dmax = 0.0, zm = 0.0;
         int bad = 0;
-        for (int64_t i = tid; i < n; i += nt) {
-            const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
-            V yr, yi, wr, wi;
+        using PU = typename std::conditional<std::is_same<E, HybridEngine<false>>::value, OutlinedHybrid<P>, P>::type;
+        if (split) {
+            // Two threads per root: the upper half of the block runs the product
+            // chains and leaves them in the root's next-iterate slot, the lower half
+            // runs the Horner chains and then finishes the roots.  Each warp carries
+            // one chain instead of two, and every chain keeps its order.
+            const int half = nt / 2;
+            if (tid >= half && tid - half < n) {
+                const int64_t i = tid - half;
+                const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
+                V dr = vone<P>(), di = vzero<P>();
+                long long Ed = 0;
+                E g;
+                for (int64_t j = 0; j < n; j++)
+                    if (j != i) dk_product_step<PU>(z, zc, j, zr, zi, dr, di, Ed, g);
+                vstore<P>(zn, pn, i, dr);
+                vstore<P>(zn + K * pn, pn, i, di);
+                sh.split_e[i] = Ed;
+                sh.split_bad[i] = g.failed() ? 1 : 0;
+            }
+            V zr = vzero<P>(), zi = vzero<P>(), hr = vzero<P>(), hi = vzero<P>();
+            long long Eq = 0;
             E g;
-            using PU = typename std::conditional<std::is_same<E, HybridEngine<false>>::value, OutlinedHybrid<P>, P>::type;
-            dk_update<PU>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
-            if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
-            vstore<P>(zn, pn, i, yr);
-            vstore<P>(zn + K * pn, pn, i, yi);
-            const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
-            const double m = __dadd_rn(fabs(yr.c[0]), fabs(yi.c[0]));
-            if (!(d == d) || isinf(d) || !(m == m) || isinf(m)) bad = 1;
-            if (d > dmax) dmax = d;
-            if (m > zm) zm = m;
+            if (tid < n) {
+                zr = vload<P>(z, zc, tid);
+                zi = vload<P>(z + K * zc, zc, tid);
+                hr = vload<P>(c, cap, n);
+                for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_step<PU>(c, cap, kk, zr, zi, hr, hi, Eq, g);
+            }
+            __syncthreads();  // the products are in place
+            if (tid < n) {
+                const int64_t i = tid;
+                const V dr = vload<P>(zn, pn, i), di = vload<P>(zn + K * pn, pn, i);
+                V yr, yi, wr, wi;
+                dk_finish<PU>(hr, hi, Eq, dr, di, sh.split_e[i], zr, zi, yr, yi, wr, wi, g);
+                if (g.failed() || sh.split_bad[i]) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                vstore<P>(zn, pn, i, yr);
+                vstore<P>(zn + K * pn, pn, i, yi);
+                const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
+                const double m = __dadd_rn(fabs(yr.c[0]), fabs(yi.c[0]));
+                if (!(d == d) || isinf(d) || !(m == m) || isinf(m)) bad = 1;
+                if (d > dmax) dmax = d;
+                if (m > zm) zm = m;
+            }
+        } else {
+            for (int64_t i = tid; i < n; i += nt) {
+                const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
+                V yr, yi, wr, wi;
+                E g;
+                dk_update<PU>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
+                if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                vstore<P>(zn, pn, i, yr);
+                vstore<P>(zn + K * pn, pn, i, yi);
+                const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
+                const double m = __dadd_rn(fabs(yr.c[0]), fabs(yi.c[0]));
+                if (!(d == d) || isinf(d) || !(m == m) || isinf(m)) bad = 1;
+                if (d > dmax) dmax = d;
+                if (m > zm) zm = m;
+            }
         }
         block_max2(sh, dmax, zm, bad);  // barrier: every read of the current iterate is done
         for (int64_t i = tid; i < n; i += nt)  // each thread copies back the roots it wrote
@@ -572,7 +649,7 @@ template <class P> static size_t dk_smem_bytes(int32_t max_degree)
     return (size_t)P::K * sizeof(double) * ((size_t)(max_degree + 1) + 2 * (size_t)max_degree);
 }
 
-constexpr size_t DK_SMEM_LIMIT = 227 * 1024 - 2048;  // leaves room for the static DKShared
+constexpr size_t DK_SMEM_LIMIT = 227 * 1024 - 4096;  // leaves room for the static DKShared
 
 template <class P> static int32_t dk_max_degree()
 {
