@@ -292,6 +292,14 @@ def gemm_traffic(prec, n, hybrid):
     return None
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def fp64_peak_live():
     import paper_2603_14926_gb300 as mpg
 
@@ -340,6 +348,23 @@ def extras(prec="qd", quick=False):
     t = timed(lambda: mpg.dot(prec, x, y, out=r, ws=ws))
     out["dot"] = {"n": n, "ms": t * 1e3, **rates(n * ins, n * ins_paper, t)}
     del x, y
+    # binary32 components: AXPY and dot are bound by HBM, not by the FP32 pipe
+    hbm = measured_hbm_gbs()
+    for p32 in ("ds", "qf"):
+        K32 = mpg.PRECS[p32][0]
+        n32 = 1 << 26
+        x32 = dev(inputs.mp_uniform(1, n32, K32, np.float32, stream=inputs.STREAM_X))
+        y32 = dev(inputs.mp_uniform(1, n32, K32, np.float32, stream=inputs.STREAM_Y))
+        ta = timed(lambda: mpg.axpy(p32, [0.5] + [0.0] * (K32 - 1), x32, y32))
+        ws32 = torch.empty(mpg.dot_workspace(p32, n32), dtype=torch.uint8, device="cuda")
+        r32 = mpg.empty(p32)
+        td = timed(lambda: mpg.dot(p32, x32, y32, out=r32, ws=ws32))
+        ab, db = 3 * K32 * 4 * n32, 2 * K32 * 4 * n32  # AXPY reads x, y and writes y; dot reads x, y
+        out[f"axpy_{p32}"] = {"n": n32, "ms": ta * 1e3, "GB/s": ab / ta / 1e9,
+                              "hbm_frac_of_measured": ab / ta / 1e9 / hbm if hbm else None}
+        out[f"dot_{p32}"] = {"n": n32, "ms": td * 1e3, "GB/s": db / td / 1e9,
+                             "hbm_frac_of_measured": db / td / 1e9 / hbm if hbm else None}
+        del x32, y32, ws32
     m = 8192
     A = dev(inputs.mp_uniform(2, (m, m), K))
     xv = dev(inputs.mp_uniform(3, m, K, stream=inputs.STREAM_X))

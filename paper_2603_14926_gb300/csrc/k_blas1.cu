@@ -176,6 +176,35 @@ template <class P> static int64_t dot_blocks(int64_t n)
     return g < 1 ? 1 : g;
 }
 
+// A thread's share of the dot: elements i0, i0 + stride, ...  Binary64 components
+// (FP64-pipe bound) fold them into one accumulator; binary32 components, whose
+// FP32 pipe is fast enough for the add chain's latency to show, fold them
+// round-robin into DOT_ACC accumulators combined in order at the end -- a fixed
+// order, so the result is still deterministic and within the same bound.
+constexpr int DOT_ACC = 4;
+
+template <class P, class E>
+__device__ __forceinline__ typename P::V dot_fold(int64_t n, const typename P::T *__restrict__ x, int64_t px,
+                                                  const typename P::T *__restrict__ y, int64_t py, int64_t i0,
+                                                  int64_t stride, E &g)
+{
+    using V = typename P::V;
+    constexpr int NA = P::fp64 ? 1 : DOT_ACC;
+    V acc[NA];
+#pragma unroll
+    for (int a = 0; a < NA; a++) acc[a] = vzero<P>();
+    int64_t i = i0;
+    for (; i + (NA - 1) * stride < n; i += NA * stride)
+#pragma unroll
+        for (int a = 0; a < NA; a++)
+            acc[a] = P::add(acc[a], P::mul(vload<P>(x, px, i + a * stride), vload<P>(y, py, i + a * stride), g), g);
+    for (int a = 0; i < n; i += stride, a++)
+        acc[a] = P::add(acc[a], P::mul(vload<P>(x, px, i), vload<P>(y, py, i), g), g);
+#pragma unroll
+    for (int a = 1; a < NA; a++) acc[0] = P::add(acc[0], acc[a], g);
+    return acc[0];
+}
+
 template <class P>
 __global__ void __launch_bounds__(DOT_THREADS) k_dot_partial(int64_t n, const typename P::T *__restrict__ x,
                                                              int64_t px, const typename P::T *__restrict__ y,
@@ -183,12 +212,11 @@ __global__ void __launch_bounds__(DOT_THREADS) k_dot_partial(int64_t n, const ty
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    typename P::V acc = vzero<P>();
     FastEngine<P> g;
-    for (int64_t i = i0; i < n; i += stride) acc = P::add(acc, P::mul(vload<P>(x, px, i), vload<P>(y, py, i), g), g);
+    typename P::V acc = dot_fold<P>(n, x, px, y, py, i0, stride, g);
     if (g.failed()) {  // the thread's fold again on the FP64 pipe
-        acc = vzero<P>();
-        for (int64_t i = i0; i < n; i += stride) acc = P::add(acc, P::mul(vload<P>(x, px, i), vload<P>(y, py, i)));
+        NativeEngine<typename P::T> nat;
+        acc = dot_fold<P>(n, x, px, y, py, i0, stride, nat);
     }
     acc = block_reduce<P>(acc);
     if (threadIdx.x == 0) vstore<P>(part, gridDim.x, blockIdx.x, acc);
