@@ -83,8 +83,9 @@ static mp_status ew_launch(int64_t n, const typename P::T *a, int64_t pa, const 
 // AXPY: y_i = add(mul(alpha, x_i), y_i)
 // ---------------------------------------------------------------------------
 
+// At least 2 (QD), 3 (three components) or 4 (two) blocks of 256 threads per SM.
 template <class P>
-__global__ void __launch_bounds__(256) k_axpy(int64_t n, typename P::V alpha,
+__global__ void __launch_bounds__(256, P::K == 4 ? 2 : (P::K == 3 ? 3 : 4)) k_axpy(int64_t n, typename P::V alpha,
                                               const typename P::T *__restrict__ x, int64_t px,
                                               typename P::T *__restrict__ y, int64_t py)
 {

@@ -60,6 +60,27 @@ MP_HD int clz64(uint64_t x)
 #endif
 }
 
+MP_HD int clz32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __clz((int)x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+MP_HD int imax(int a, int b) { return a > b ? a : b; }
+
+// high word of (hi:lo) << min(c, 32)
+MP_HD uint32_t shl_hi(uint32_t lo, uint32_t hi, uint32_t c)
+{
+#ifdef __CUDA_ARCH__
+    return __funnelshift_lc(lo, hi, c);
+#else
+    return c >= 32 ? lo : c == 0 ? hi : (hi << c) | (lo >> (32 - c));
+#endif
+}
+
 // low word of (hi:lo) >> 11
 MP_HD uint32_t shr11_lo(uint32_t lo, uint32_t hi)
 {
@@ -98,23 +119,36 @@ MP_HD uint64_t two_sum_err(uint64_t A, uint64_t B, uint64_t S, uint32_t &bad)
     unpack(B, eb, mb);
     unpack(S, es, ms);
     const int u = imin(imin(ea, eb), es);
-    uint64_t ta = shl_mod(ma, (uint32_t)(ea - u)), tb = shl_mod(mb, (uint32_t)(eb - u));
+    const uint64_t ta = shl_mod(ma, (uint32_t)(ea - u)), tb = shl_mod(mb, (uint32_t)(eb - u));
     const uint64_t ts = shl_mod(ms, (uint32_t)(es - u));
-    // conditional negation by the sign words: (t ^ k) - k with k = 0 or all ones
+    // Signs by the sign words k = 0 or all ones: (t ^ k) - k negates t when k is all
+    // ones, and -x = ~x + 1, so
+    //   ei = (ta^ka) - ka + (tb^kb) - kb - ((ts^ks) - ks)
+    //      = (ta^ka) + (tb^kb) + (ts^~ks) + (1 + ks - ka - kb),
+    // the last term a small constant in [0, 3].
     const uint64_t ka = (uint64_t)((int64_t)A >> 63), kb = (uint64_t)((int64_t)B >> 63),
                    ks = (uint64_t)((int64_t)S >> 63);
-    ta = (ta ^ ka) - ka;
-    tb = (tb ^ kb) - kb;
-    const uint64_t ei = ta + tb - ((ts ^ ks) - ks);
+    const uint32_t cc = 1u + lo32(ks) - lo32(ka) - lo32(kb);
+    const uint64_t ei = (ta ^ ka) + (tb ^ kb) + (ts ^ ~ks) + (uint64_t)cc;
     const uint64_t kn = (uint64_t)((int64_t)ei >> 63);
     const uint64_t mag = (ei ^ kn) - kn;
-    const int lz = clz64(mag);
-    const uint64_t norm = shl_mod(mag, (uint32_t)lz & 63u);  // leading one at bit 63
-    const int be = 11 - lz + u;                               // biased exponent of e
-    const uint32_t eh = ((hi32(norm) >> 11) + ((uint32_t)(be - 1) << 20)) | (hi32(kn) & 0x80000000u);
-    const uint32_t el = shr11_lo(lo32(norm), hi32(norm));
-    bad |= (uint32_t)(ea > 2045) | (uint32_t)(eb > 2045) | (uint32_t)(es > 2046) | (uint32_t)(mag != 0 && be < 1);
-    return mag == 0 ? 0 : mk64(eh, el);
+    // Normalise mag (< 2^55) to a leading one at bit 63 with one count-leading-zeros:
+    // on the high word when it is nonzero, else on the low word (then lz = 32 + c).
+    const uint32_t mh = hi32(mag), ml = lo32(mag);
+    const bool z = mh == 0;
+    const uint32_t x = z ? ml : mh, y = z ? 0u : ml;
+    const int c = clz32(x);                          // 32 only when mag == 0
+    const uint32_t nh = shl_hi(y, x, (uint32_t)c);   // high word of mag << lz (0 when mag == 0)
+    const uint32_t nl = y << (c & 31);               // low word (y == 0 whenever c == 32)
+    const int be = 11 - c - (z ? 32 : 0) + u;        // biased exponent of e
+    // The hidden bit (bit 20 of nh >> 11) is 2^20 exactly when mag != 0, so multiplying
+    // the exponent field by it packs +0 for mag == 0 with no select.
+    const uint32_t f = nh >> 11, hb = f & 0x100000u;
+    const uint32_t eh = (f + (uint32_t)(be - 1) * hb) | (hi32(kn) & 0x80000000u);
+    const uint32_t el = shr11_lo(nl, nh);
+    // |s| <= 2 max(|a|, |b|), so exponents of a and b <= 2045 bound s's by 2046
+    bad |= (uint32_t)(imax(ea, eb) > 2045) | (uint32_t)(hb != 0 && be < 1);
+    return mk64(eh, el);
 }
 
 // e = a*b - p for p = fl(a*b) (the error term of Algorithm 3's TwoProd, which
