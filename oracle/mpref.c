@@ -148,6 +148,12 @@ double mpref_dk_nthroot(double v, int64_t m) { return dk_nthroot(v, m); }
         MPREF_CAT(cgemm3m, SFXV)(&PV, opA, opB, m, n, k, Ar, Ai, lda, pA, Br, Bi, ldb, pB,   \
                                  Cr, Ci, ldc, pC);                                          \
     }                                                                                       \
+    void mpref_gemm_strassen_##S(int64_t m, int64_t n, int64_t k, const T *A, int64_t lda,     \
+                                 int64_t pA, const T *B, int64_t ldb, int64_t pB, T *C,      \
+                                 int64_t ldc, int64_t pC, int64_t cutoff)                    \
+    {                                                                                       \
+        MPREF_CAT(strassen, SFXV)(&PV, m, n, k, A, lda, pA, B, ldb, pB, C, ldc, pC, cutoff); \
+    }                                                                                       \
     void mpref_polyeval_##S(int64_t npoly, const int64_t *coef_off, const T *coef,          \
                             int64_t pcoef, int64_t npts, const T *x_re, const T *x_im,      \
                             int64_t px, T *y_re, T *y_im, int64_t py)                       \

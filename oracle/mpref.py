@@ -129,6 +129,7 @@ def _declare(L):
                      _i64, _vp, _i64, _i64],
             "cgemm": [ctypes.c_int, ctypes.c_int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp,
                       _i64, _i64, _vp, _vp, _i64, _i64],
+            "gemm_strassen": [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _i64],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64],
             "polyeval_estrin": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -277,6 +278,20 @@ def gemm(prec, A, B, opA=0, opB=0, rows=None):
             Ap = A.ctypes.data + r0 * lda * A.itemsize
         getattr(lib(), f"mpref_gemm_{prec}")(opA, opB, r1 - r0, n, k, _vp(Ap), lda, A[0].size,
                                              _p(B), ldb, B[0].size, _p(C), n, C[0].size)
+    return C
+
+
+def gemm_strassen(prec, A, B, cutoff=32):
+    """C := A B by Strassen's recursion (Section 3.1): classical fold below `cutoff`,
+    quadrants zero-padded to ceil(size/2) where a dimension is odd."""
+    A, B = _arr(A, prec), _arr(B, prec)
+    K, m, k = A.shape
+    k2, n = B.shape[1], B.shape[2]
+    assert k == k2 and cutoff >= 2
+    C = np.zeros((K, m, n), dtype=A.dtype)
+    if m and n:
+        getattr(lib(), f"mpref_gemm_strassen_{prec}")(m, n, k, _p(A), k, max(A[0].size, 1), _p(B), n,
+                                                      max(B[0].size, 1), _p(C), n, C[0].size, cutoff)
     return C
 
 

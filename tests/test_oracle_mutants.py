@@ -4,7 +4,8 @@ that its pins catch every one.
 Each mutant edits one line of the oracle's C source: a wrong operand, TwoSum
 swapped for QuickTwoSum, a dropped term, a swapped component index, a sign
 slip, transposed GEMM indices, an off-by-one Horner coefficient, a Newton sign
-error, a Durand-Kerner product that includes j = i, a mis-wired Estrin tree.
+error, a Durand-Kerner product that includes j = i, a mis-wired Estrin tree, a
+Strassen product, combination or quadrant gone wrong.
 The pin battery below
 (exact rationals, the op counts of Tables 1 and 2, error bounds, identities,
 permutation GEMM, known roots) must pass on the real oracle and fail on every
@@ -56,6 +57,11 @@ MUTANTS = [
     ("Estrin lost pass-through", CORE, "                vr[4 * half + c] = vr[4 * (len - 1) + c];",
      "                vr[4 * half + c] = 0;"),
     ("Estrin power doubled, not squared", CORE, "                P->mul(pr, pr, pr);", "                P->add(pr, pr, pr);"),
+    ("Strassen M4 operands swapped", CORE, "T = F(msum)(P, B21, B11, nb, 1);", "T = F(msum)(P, B11, B21, nb, 1);"),
+    ("Strassen C22 sign", CORE, "F(load)(P, M[2], nc, t, b); F(mp_sub)(P, a, b, a);",
+     "F(load)(P, M[2], nc, t, b); P->add(a, b, a);"),
+    ("Strassen quadrant offset", CORE, "*A21 = F(block)(P, A, lda, pA, m, k, hm, 0, hm, hk)",
+     "*A21 = F(block)(P, A, lda, pA, m, k, hm - 1, 0, hm, hk)"),
     ("DK product includes j == i", DK, "                if (j == i) continue;\n                load_d(P, z, pz, j, zjr);",
      "                load_d(P, z, pz, j, zjr);"),
     ("DK wrong update sign", DK, "            mp_sub_d(P, zr, wr, yr);", "            P->add(zr, wr, yr);"),
@@ -152,6 +158,14 @@ def _blas_poly(oracle, bad):
     want = np.zeros_like(A)
     want[:, :, perm] = A
     check("GEMM permutation", np.array_equal(oracle.gemm("qd", A, Pm), want))
+    # Strassen on integer matrices (odd sizes, three levels): exact
+    rng = np.random.default_rng(12)
+    Ai = np.zeros((K, 13, 11))
+    Bi = np.zeros((K, 11, 9))
+    Ai[0] = rng.integers(-40, 41, (13, 11))
+    Bi[0] = rng.integers(-40, 41, (11, 9))
+    Cs = oracle.gemm_strassen("qd", Ai, Bi, 3)
+    check("Strassen exact", np.array_equal(Cs[0], Ai[0] @ Bi[0]) and not Cs[1:].any())
     # Horner vs exact
     off = np.array([0, 9], dtype=np.int64)
     coef = inputs.mp_uniform(3, 9, K, stream=inputs.STREAM_C)
