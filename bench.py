@@ -457,6 +457,31 @@ def extras(prec="qd", quick=False):
                               "fp32_instr_frac_of_nominal": n2 ** 3 * mac_instr(p2) / t2 / fp32_peak}
         del A2, B2, C2
     out["gemm_sizes"] = grid
+    # Strassen's recursion (Section 3.1's scheme) on the QD GEMM: 7^L leaf GEMMs of
+    # size n / 2^L plus 18 elementwise sums per node, against the classical fold
+    runs = ((1024, 1024),) if quick else ((2048, 2048), (4096, 4096), (4096, 2048))
+    strassen = {}
+    for i, (n2, cut) in enumerate(runs):
+        A2 = dev(inputs.mp_uniform(2, (n2, n2), K, stream=inputs.STREAM_A))
+        B2 = dev(inputs.mp_uniform(2, (n2, n2), K, stream=inputs.STREAM_B))
+        C2 = mpg.empty(prec, n2, n2)
+        ws2 = torch.empty(max(mpg.gemm_strassen_workspace(prec, n2, n2, n2, cut), 1), dtype=torch.uint8,
+                          device="cuda")
+        t2 = timed(lambda: mpg.gemm_strassen(prec, A2, B2, cut, out=C2, ws=ws2), reps=1, warm=i == 0)
+        L, h, sums = 0, n2, 0
+        while h >= cut:
+            h = (h + 1) // 2
+            sums += 7 ** L * 18 * h * h
+            L += 1
+        macs = 7 ** L * h ** 3
+        cls = grid.get(f"{prec}_{n2}", {}).get("ms")
+        strassen[f"n{n2}_cutoff{cut}"] = {
+            "levels": L, "leaf": h, "ms": t2 * 1e3, "classical_ms": cls,
+            "speedup_over_classical": cls / (t2 * 1e3) if cls else None,
+            "classical_equiv_qd_ops_per_s": 2.0 * n2 ** 3 / t2,
+            **rates(macs * ins + sums * add_instr(prec), macs * ins_paper + sums * INSTR_ADD[prec], t2)}
+        del A2, B2, C2, ws2
+    out["gemm_strassen"] = strassen
     return out
 
 

@@ -184,6 +184,33 @@ const char *mp_version(void);
                            void *ws, size_t ws_bytes, mp_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* GEMM_STRASSEN  real C := A B by Strassen's recursion, the matrix         */
+/* multiplication scheme of Section 3.1 (the paper recurses until the       */
+/* submatrices drop below 32 x 32), with Strassen's seven products:         */
+/*   M1 = (A11+A22)(B11+B22)  M2 = (A21+A22)B11  M3 = A11(B12-B22)          */
+/*   M4 = A22(B21-B11)  M5 = (A11+A12)B22  M6 = (A21-A11)(B11+B12)           */
+/*   M7 = (A12-A22)(B21+B22)                                                */
+/*   C11 = ((M1+M4)-M5)+M7  C12 = M3+M5  C21 = M2+M4  C22 = ((M1-M2)+M3)+M6 */
+/* A node with min(m, n, k) < cutoff is one classical GEMM (mp_gemm_ex_P,   */
+/* sequential k).  Otherwise quadrants are ceil(m/2) x ceil(k/2) (A) and     */
+/* ceil(k/2) x ceil(n/2) (B) blocks, zero-padded where a dimension is odd;  */
+/* sums and differences are elementwise multicomponent adds (a difference    */
+/* adds the negated operand), a padded entry taking part as +0; C keeps the */
+/* unpadded part.  Bit-identical to the CPU oracle for the same cutoff.     */
+/* No transposes: A is m x k (lda, pA), B is k x n (ldb, pB), row-major     */
+/* K-arrays as for GEMM.  cutoff >= 2 (else MP_EINVAL).                      */
+/* ws: DEVICE workspace of mp_gemm_strassen_workspace_P(m, n, k, cutoff)     */
+/* bytes (three buffers per recursion level; 0 when no level recurses; no   */
+/* initialisation needed); MP_ENOMEM if smaller.  C must not overlap A, B.   */
+/* ------------------------------------------------------------------------ */
+#define MPGPU_DECL_STRASSEN(P, T)                                                           \
+    size_t mp_gemm_strassen_workspace_##P(int64_t m, int64_t n, int64_t k, int64_t cutoff); \
+    mp_status mp_gemm_strassen_##P(int64_t m, int64_t n, int64_t k, const T *A, int64_t lda, \
+                                   int64_t pA, const T *B, int64_t ldb, int64_t pB, T *C,   \
+                                   int64_t ldc, int64_t pC, int64_t cutoff, void *ws,       \
+                                   size_t ws_bytes, mp_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* POLYEVAL  (Section 4.1) batched Horner evaluation of real-coefficient    */
 /* polynomials p_b(x) = sum_{i=0}^{n_b} a_{b,i} x^i.                        */
 /*   coef_off : DEVICE int64[npoly+1]; polynomial b owns coefficients        */
@@ -340,6 +367,7 @@ typedef struct {
     MPGPU_DECL_GEMV(P, T)                                                                   \
     MPGPU_DECL_GEMM(P, T)                                                                   \
     MPGPU_DECL_CGEMM(P, T)                                                                  \
+    MPGPU_DECL_STRASSEN(P, T)                                                               \
     MPGPU_DECL_POLY(P, T)
 
 MPGPU_DECL_ALL(dd, double)

@@ -1,6 +1,7 @@
 /*
  * mpref.c -- CPU oracle for branch-free multicomponent arithmetic
- * (Kouya, arXiv 2603.14926: Algorithms 1-14, Section 3 GEMM, Section 4
+ * (Kouya, arXiv 2603.14926: Algorithms 1-14, Section 3 GEMM (classical fold,
+ * Strassen's recursion, 3M complex), Section 4
  * polynomial evaluation and the Durand-Kerner solver).
  *
  * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, scalar restatement of the

@@ -72,6 +72,8 @@ def _declare(L):
                         _i64, _i64, _int, _vp],
             "cgemm": [_int, _int, _i64, _i64, _i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _i64,
                       _vp, _vp, _i64, _i64, _vp, ctypes.c_size_t, _vp],
+            "gemm_strassen": [_i64, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _i64,
+                              _i64, _vp, ctypes.c_size_t, _vp],
             "polyeval": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
             "polyeval_estrin": [_i64, _vp, _vp, _i64, _i64, _vp, _vp, _i64, _vp, _vp, _i64, _vp],
             "polyeval_backward": [_i64, _vp, _vp, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -89,6 +91,8 @@ def _declare(L):
         getattr(L, f"mp_polyeval_backward_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_cgemm_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
         getattr(L, f"mp_cgemm_workspace_{p}").restype = ctypes.c_size_t
+        getattr(L, f"mp_gemm_strassen_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
+        getattr(L, f"mp_gemm_strassen_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int
         getattr(L, f"mp_gemm_tma_timeouts_{p}").argtypes = [ctypes.POINTER(ctypes.c_uint)]
         getattr(L, f"mp_gemm_tma_timeouts_{p}").restype = _int
@@ -321,6 +325,29 @@ def gemm(prec, A, B, opA=0, opB=0, out=None, config=None):
           _ptr(B), B[0].stride(0), _ps(B), _ptr(out), out[0].stride(0), _ps(out), int(config),
           _stream())
     return out
+
+
+def gemm_strassen_workspace(prec, m, n, k, cutoff=32):
+    return int(getattr(lib(), f"mp_gemm_strassen_workspace_{prec}")(m, n, k, cutoff))
+
+
+def gemm_strassen(prec, A, B, cutoff=32, out=None, ws=None):
+    """Real C := A B by Strassen's recursion (classical GEMM below `cutoff`,
+    zero-padded quadrants for odd sizes); A (K, m, k), B (K, k, n)."""
+    t = _torch()
+    _check(prec, A, "A", 3)
+    _check(prec, B, "B", 3)
+    m, k = A.shape[1], A.shape[2]
+    k2, n = B.shape[1], B.shape[2]
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {k} vs {k2}")
+    C = out if out is not None else empty(prec, m, n, device=A.device)
+    nb = gemm_strassen_workspace(prec, m, n, k, cutoff)
+    if ws is None:
+        ws = t.empty(max(nb, 1), dtype=t.uint8, device=A.device)
+    _call(f"mp_gemm_strassen_{prec}", m, n, k, _ptr(A), A[0].stride(0), _ps(A), _ptr(B), B[0].stride(0),
+          _ps(B), _ptr(C), C[0].stride(0), _ps(C), int(cutoff), _ptr(ws), ws.numel(), _stream())
+    return C
 
 
 def cgemm(prec, Ar, Ai, Br, Bi, opA=0, opB=0, out=None, ws=None):

@@ -42,7 +42,7 @@ def units():
     out = [("k_blas1.o", "k_blas1.cu", [])]
     for p in GEMM_PRECS:
         out.append((f"k_gemm_{p}.o", "k_gemm.cu", [f"-DMPGPU_GEMM_PREC={p}"]))
-    for extra in ("k_poly.cu", "k_roots.cu", "k_cgemm.cu"):
+    for extra in ("k_poly.cu", "k_roots.cu", "k_cgemm.cu", "k_strassen.cu"):
         if os.path.exists(os.path.join(CSRC, extra)):
             out.append((extra.replace(".cu", ".o"), extra, []))
     return out
