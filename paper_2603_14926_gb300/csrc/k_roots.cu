@@ -460,6 +460,16 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     __syncthreads();
 
     const bool split = nt % 64 == 0 && n <= nt / 2 && n <= DK_SPLIT_MAX;
+    // Product chains of a split sweep start 64 threads (two warps) after the Horner
+    // chains when both fit in two warps each, else at the block's upper half: the
+    // two chains of a root then run on different SM sub-partitions (warp w issues
+    // on sub-partition w mod 4).
+    const int poff = (n <= 64 && nt >= 128) ? 64 : nt / 2;
+    // Roots are dealt to threads from a warp offset that rotates with the
+    // polynomial and the sweep, so the partial last round of a sweep (and the
+    // chains of a small polynomial) does not always load the same warps -- the
+    // same sub-partitions -- of every block.  Each root's arithmetic is unchanged.
+    const int nwarps = nt % 32 == 0 ? nt / 32 : 0;
     const long long t0 = clock64();
     int st = DK_CAP, it = A.max_iter;
     double best = __longlong_as_double(0x7ff0000000000000LL);  // +inf
@@ -467,15 +477,16 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     for (int k = 1; k <= A.max_iter; k++) {
         double dmax = 0.0, zm = 0.0;
         int bad = 0;
+        const int rot = nwarps > 1 ? 32 * (int)((b + k) % nwarps) : 0;
+        const int vt = (tid + nt - rot) % nt;  // this thread's place in the dealing order
         using PU = typename std::conditional<std::is_same<E, HybridEngine<false>>::value, OutlinedHybrid<P>, P>::type;
         if (split) {
-            // Two threads per root: the upper half of the block runs the product
-            // chains and leaves them in the root's next-iterate slot, the lower half
-            // runs the Horner chains and then finishes the roots.  Each warp carries
-            // one chain instead of two, and every chain keeps its order.
-            const int half = nt / 2;
-            if (tid >= half && tid - half < n) {
-                const int64_t i = tid - half;
+            // Two threads per root: places poff .. poff+n-1 of the dealing order run
+            // the product chains and leave them in the root's next-iterate slot,
+            // places 0 .. n-1 run the Horner chains and then finish the roots.  Each
+            // warp carries one chain instead of two, and every chain keeps its order.
+            if (vt >= poff && vt - poff < n) {
+                const int64_t i = vt - poff;
                 const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
                 V dr = vone<P>(), di = vzero<P>();
                 long long Ed = 0;
@@ -490,15 +501,15 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
             V zr = vzero<P>(), zi = vzero<P>(), hr = vzero<P>(), hi = vzero<P>();
             long long Eq = 0;
             E g;
-            if (tid < n) {
-                zr = vload<P>(z, zc, tid);
-                zi = vload<P>(z + K * zc, zc, tid);
+            if (vt < n) {
+                zr = vload<P>(z, zc, vt);
+                zi = vload<P>(z + K * zc, zc, vt);
                 hr = vload<P>(c, cap, n);
                 for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_step<PU>(c, cap, kk, zr, zi, hr, hi, Eq, g);
             }
             __syncthreads();  // the products are in place
-            if (tid < n) {
-                const int64_t i = tid;
+            if (vt < n) {
+                const int64_t i = vt;
                 const V dr = vload<P>(zn, pn, i), di = vload<P>(zn + K * pn, pn, i);
                 V yr, yi, wr, wi;
                 dk_finish<PU>(hr, hi, Eq, dr, di, sh.split_e[i], zr, zi, yr, yi, wr, wi, g);
@@ -512,7 +523,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
                 if (m > zm) zm = m;
             }
         } else {
-            for (int64_t i = tid; i < n; i += nt) {
+            for (int64_t i = vt; i < n; i += nt) {
                 const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
                 V yr, yi, wr, wi;
                 E g;
@@ -528,7 +539,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
             }
         }
         block_max2(sh, dmax, zm, bad);  // barrier: every read of the current iterate is done
-        for (int64_t i = tid; i < n; i += nt)  // each thread copies back the roots it wrote
+        for (int64_t i = tid; i < n; i += nt)  // copy back (after the barrier any thread may)
             for (int cc = 0; cc < 2 * K; cc++) z[cc * zc + i] = zn[cc * pn + i];
         __syncthreads();
         const double delta = sh.delta, zmax = sh.zmax;
