@@ -755,7 +755,9 @@ def profile_one(a):
         print(json.dumps({"lane_instr_per_s_G": res, "lanes_per_clk_per_sm_at_max_clock": per_sm_clk, "sms": sms}))
         return
     elif a.profile == "dk":
-        prob = inputs.dk_problem(3, a.n, 10, 500)
+        # mixed degrees 10..500 (the batched-root workload), or one degree for all
+        prob = inputs.dk_problem(3, a.n, 10, 500) if a.dk_degree <= 0 else \
+            inputs.dk_problem(5, a.n, a.dk_degree, a.dk_degree)
         md = int(prob.degrees.max())
         coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), md,
                                    int(prob.coef_off[-1]))
@@ -903,6 +905,8 @@ def main(argv=None):
     ap.add_argument("--dk-engine", type=int, default=0, choices=[0, 1, 2],
                     help="Durand-Kerner engine for --workload roots and --profile dk: 0 automatic (hybrid), "
                          "1 hybrid, 2 FP64 pipe")
+    ap.add_argument("--dk-degree", type=int, default=0,
+                    help="--profile dk: give every polynomial this degree (0: degrees uniform in [10, 500])")
     ap.add_argument("--profile", choices=["gemm", "horner", "dcoef", "dk", "peak"], default=None,
                     help="run one launch of this kernel family at size --n (for ncu) and exit")
     a = ap.parse_args(argv)
