@@ -187,6 +187,72 @@ def _oracle_rows(args):
     return time.perf_counter() - t
 
 
+def _oracle_row_rates(_=None):
+    """Worker: the oracle, as it stands, on ONE host core over a bounded sample of
+    each hot-path row's workload (QD), in the units bench.py reports for the GPU."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from oracle import mpref as o
+    from paper_2603_14926_gb300 import inputs
+
+    K = 4
+    out = {}
+
+    def timed(fn):
+        t = time.perf_counter()
+        fn()
+        return time.perf_counter() - t
+
+    n = 1 << 19
+    x = inputs.mp_uniform(1, n, K, stream=inputs.STREAM_X)
+    y = inputs.mp_uniform(1, n, K, stream=inputs.STREAM_Y)
+    alpha = inputs.mp_uniform(2, 1, K)[:, 0]
+    t = timed(lambda: o.axpy("qd", alpha, x, y))
+    out["axpy"] = {"elements_per_s": n / t, "sample": f"n = {n}"}
+    t = timed(lambda: o.dot("qd", x, y))
+    out["dot"] = {"elements_per_s": n / t, "sample": f"n = {n}"}
+    m, k = 64, 8192
+    A = inputs.mp_uniform(2, (m, k), K)
+    xv = inputs.mp_uniform(3, k, K, stream=inputs.STREAM_X)
+    t = timed(lambda: o.gemv("qd", A, xv))
+    out["gemv"] = {"mac_per_s": m * k / t, "sample": f"{m} rows of 8192 x 8192"}
+    deg, npts, npoly = 256, 512, 8
+    off = np.arange(0, (npoly + 1) * (deg + 1), deg + 1, dtype=np.int64)
+    coef = inputs.mp_uniform(4, npoly * (deg + 1), K, stream=inputs.STREAM_C)
+    xs = inputs.mp_uniform(5, npoly * npts, K, stream=inputs.STREAM_X)
+    dy = inputs.mp_uniform(6, npoly * npts, K, stream=inputs.STREAM_Y)
+    steps = npoly * npts * deg
+    t = timed(lambda: o.polyeval("qd", off, coef, npts, xs))
+    out["horner_fwd"] = {"steps_per_s": steps / t, "sample": f"{npoly} polynomials x degree {deg} x {npts} points"}
+    t = timed(lambda: o.polyeval_estrin("qd", off, coef, npts, xs))
+    out["estrin_fwd"] = {"steps_per_s": steps / t, "sample": out["horner_fwd"]["sample"]}
+    t = timed(lambda: o.polyeval_backward("qd", off, coef, npts, xs, dy))
+    out["horner_bwd"] = {"steps_per_s": steps / t, "sample": out["horner_fwd"]["sample"]}
+    nc = 128
+    Ar, Ai = inputs.mp_uniform(7, (nc, nc), K), inputs.mp_uniform(8, (nc, nc), K)
+    Br, Bi = inputs.mp_uniform(9, (nc, nc), K), inputs.mp_uniform(10, (nc, nc), K)
+    t = timed(lambda: o.cgemm("qd", Ar, Ai, Br, Bi))
+    out["complex_gemm_3m"] = {"complex_qd_ops_per_s": 8.0 * nc ** 3 / t, "sample": f"n = {nc}"}
+    ns = 192
+    As, Bs = inputs.mp_uniform(2, (ns, ns), K, stream=inputs.STREAM_A), inputs.mp_uniform(2, (ns, ns), K, stream=inputs.STREAM_B)
+    t = timed(lambda: o.gemm_strassen("qd", As, Bs, 32))
+    out["gemm_strassen"] = {"classical_equiv_qd_ops_per_s": 2.0 * ns ** 3 / t, "sample": f"n = {ns}, cutoff 32"}
+    # Durand-Kerner: a degree-stratified slice of the batched-root workload, 2 sweeps
+    prob = inputs.dk_problem(3, 4096, 10, 500)
+    sel = np.argsort(prob.degrees, kind="stable")[np.linspace(0, 4095, 8).astype(int)]
+    parts = [(prob.rootdata[prob.root_off[b]:prob.root_off[b + 1]], prob.delta[prob.root_off[b]:prob.root_off[b + 1]])
+             for b in sel]
+    sub = inputs.DKProblem(prob.degrees[sel], np.concatenate([r for r, _ in parts]),
+                           np.concatenate([d for _, d in parts]))
+    coef = o.poly_from_roots("qd", sub)
+    res = {}
+    t = timed(lambda: res.update(r=o.roots("qd", sub.coef_off, coef, radius=1.1, max_iter=2)))
+    its = res["r"][1]
+    out["durand_kerner"] = {"root_sweeps_per_s": float(np.sum(sub.degrees * its)) / t,
+                            "sample": f"degrees {sub.degrees.tolist()}, 2 sweeps"}
+    return out
+
+
 class OraclePool:
     """Process pool started before the first GPU call (spawn context)."""
 
@@ -209,6 +275,39 @@ class OraclePool:
     def close(self):
         self.pool.close()
         self.pool.join()
+
+
+def oracle_beside_gpu(pool, ex):
+    """The oracle on one host core (bounded samples, one spawned worker) beside each
+    GPU row of `ex`, with the GPU's throughput over the oracle's."""
+    o = pool.pool.apply(_oracle_row_rates)
+    def put(key, unit, gpu):
+        if key in o and gpu:
+            o[key]["gpu_" + unit] = gpu
+            o[key]["gpu_over_oracle"] = gpu / o[key][unit]
+
+    if "axpy" in ex:
+        put("axpy", "elements_per_s", ex["axpy"]["n"] / (ex["axpy"]["ms"] / 1e3))
+    if "dot" in ex:
+        put("dot", "elements_per_s", ex["dot"]["n"] / (ex["dot"]["ms"] / 1e3))
+    if "gemv" in ex:
+        put("gemv", "mac_per_s", ex["gemv"]["m"] * ex["gemv"]["n"] / (ex["gemv"]["ms"] / 1e3))
+    if "horner_fwd" in ex:
+        h = ex["horner_fwd"]
+        steps = h["polys"] * h["points"] * h["degree"]
+        put("horner_fwd", "steps_per_s", steps / (h["ms"] / 1e3))
+        if "estrin_fwd" in ex:
+            put("estrin_fwd", "steps_per_s", steps / (ex["estrin_fwd"]["ms"] / 1e3))
+        if "horner_bwd" in ex:
+            put("horner_bwd", "steps_per_s", steps / (ex["horner_bwd"]["ms"] / 1e3))
+    if "complex_gemm_3m" in ex:
+        put("complex_gemm_3m", "complex_qd_ops_per_s", ex["complex_gemm_3m"]["complex_qd_ops_per_s"])
+    if ex.get("gemm_strassen"):
+        best = max(v["classical_equiv_qd_ops_per_s"] for v in ex["gemm_strassen"].values())
+        put("gemm_strassen", "classical_equiv_qd_ops_per_s", best)
+    if "durand_kerner" in ex:
+        put("durand_kerner", "root_sweeps_per_s", ex["durand_kerner"]["root_sweeps_per_s"])
+    return o
 
 
 def cpu_cores():
@@ -849,6 +948,8 @@ def run_gpu(a, rank, world, pool):
             ex = extras(prec, quick=a.quick)
             ex["durand_kerner"] = dk_extra(prec, npoly=512 if a.quick else 4096)
             ex["chebyshev_dk"] = chebyshev_extra(prec, copies=512 if a.quick else 4096, pool=pool)
+            if pool is not None:
+                ex["oracle_one_core"] = oracle_beside_gpu(pool, ex)
             out["extra"] = ex
         except Exception as e:  # extras never hide the headline
             out["extra"] = {"error": repr(e)}
