@@ -250,6 +250,10 @@ def _oracle_row_rates(_=None):
     its = res["r"][1]
     out["durand_kerner"] = {"root_sweeps_per_s": float(np.sum(sub.degrees * its)) / t,
                             "sample": f"degrees {sub.degrees.tolist()}, 2 sweeps"}
+    # the paper's DK problem (Chebyshev, n = 64): one whole solve
+    cq = inputs.rational_to_mp(inputs.chebyshev_quadrature(64), K)
+    t = timed(lambda: o.roots("qd", np.array([0, 65]), cq))
+    out["chebyshev_dk"] = {"single_solve_s": t, "sample": "n = 64, one solve to the end"}
     return out
 
 
@@ -277,9 +281,11 @@ class OraclePool:
         self.pool.join()
 
 
-def oracle_beside_gpu(pool, ex):
-    """The oracle on one host core (bounded samples, one spawned worker) beside each
-    GPU row of `ex`, with the GPU's throughput over the oracle's."""
+def cpu_baseline_rows(pool, ex):
+    """The CPU baseline per hot-path row: the oracle on one host core (bounded
+    samples, one spawned worker) beside each GPU row of `ex`, with the GPU's
+    throughput over the oracle's (for the Chebyshev solve, the oracle's time over
+    the GPU's)."""
     o = pool.pool.apply(_oracle_row_rates)
     def put(key, unit, gpu):
         if key in o and gpu:
@@ -307,6 +313,10 @@ def oracle_beside_gpu(pool, ex):
         put("gemm_strassen", "classical_equiv_qd_ops_per_s", best)
     if "durand_kerner" in ex:
         put("durand_kerner", "root_sweeps_per_s", ex["durand_kerner"]["root_sweeps_per_s"])
+    if "chebyshev_dk" in ex and "chebyshev_dk" in o:
+        g = ex["chebyshev_dk"]["single_solve_gpu_s"]
+        o["chebyshev_dk"]["gpu_single_solve_s"] = g
+        o["chebyshev_dk"]["gpu_over_oracle"] = o["chebyshev_dk"]["single_solve_s"] / g
     return o
 
 
@@ -667,10 +677,10 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
     return res
 
 
-def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None, engine=0):
+def chebyshev_extra(prec="qd", n=64, copies=4096, engine=0):
     """The paper's Durand-Kerner problem (Section 4.2, Eq. 6, n = 64; Table 6): one solve
     on the GPU (latency), a batch of `copies` identical problems in one persistent
-    launch (throughput), and the oracle's single solve on one host core."""
+    launch (throughput); the oracle's single solve is timed in the CPU baseline."""
     import torch
 
     import paper_2603_14926_gb300 as mpg
@@ -722,23 +732,7 @@ def chebyshev_extra(prec="qd", n=64, copies=4096, pool=None, engine=0):
                            "batch_s": e0.elapsed_time(e1) / 1e3,
                            "identical_bits": bool(torch.equal(r2.view(torch.int64), r.view(torch.int64)) and
                                                   torch.equal(rb2.view(torch.int64), rb.view(torch.int64)))}
-    if pool is not None:
-        res["oracle_single_core_s"] = pool.pool.apply(_oracle_chebyshev, ((prec, n),))
     return res
-
-
-def _oracle_chebyshev(args):
-    prec, n = args
-    if ROOT not in sys.path:
-        sys.path.insert(0, ROOT)
-    from oracle import mpref
-    from paper_2603_14926_gb300 import inputs
-
-    K = mpref.PRECS[prec][0]
-    c = inputs.rational_to_mp(inputs.chebyshev_quadrature(n), K)
-    t = time.perf_counter()
-    mpref.roots(prec, np.array([0, n + 1]), c)
-    return time.perf_counter() - t
 
 
 def roots_workload(a):
@@ -947,9 +941,9 @@ def run_gpu(a, rank, world, pool):
         try:
             ex = extras(prec, quick=a.quick)
             ex["durand_kerner"] = dk_extra(prec, npoly=512 if a.quick else 4096)
-            ex["chebyshev_dk"] = chebyshev_extra(prec, copies=512 if a.quick else 4096, pool=pool)
-            if pool is not None:
-                ex["oracle_one_core"] = oracle_beside_gpu(pool, ex)
+            ex["chebyshev_dk"] = chebyshev_extra(prec, copies=512 if a.quick else 4096)
+            if pool is not None and "cpu_baseline" in out:
+                out["cpu_baseline"]["rows_one_core"] = cpu_baseline_rows(pool, ex)
             out["extra"] = ex
         except Exception as e:  # extras never hide the headline
             out["extra"] = {"error": repr(e)}
