@@ -1,5 +1,6 @@
-"""Multi-rank logic of bench.py on CPU: two gloo ranks, each a replica; the job
-time is the slowest rank's and the throughput counts every rank's work."""
+"""bench.py on CPU: the multi-rank logic (two gloo ranks, each a replica; the job
+time is the slowest rank's and the throughput counts every rank's work) and the
+CPU-baseline leg's per-row oracle timings."""
 
 import os
 import socket
@@ -51,3 +52,28 @@ def test_reference_arm_only_rank0(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.main(["--impl", "reference"]) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_cpu_baseline_rows_beside_gpu_rows():
+    """The CPU-baseline leg's per-row timings: the oracle on one core of a spawned
+    pool, each row in the GPU row's unit, with the GPU's rate over the oracle's."""
+    import bench
+
+    bench.oracle_build()
+    pool = bench.OraclePool(1)
+    try:
+        ex = {"axpy": {"n": 1 << 24, "ms": 3.2}, "dot": {"n": 1 << 24, "ms": 3.3},
+              "gemv": {"m": 8192, "n": 8192, "ms": 13.7},
+              "horner_fwd": {"polys": 1024, "points": 4096, "degree": 256, "ms": 200.0},
+              "estrin_fwd": {"ms": 566.0}, "horner_bwd": {"ms": 956.0},
+              "complex_gemm_3m": {"complex_qd_ops_per_s": 1.28e10},
+              "gemm_strassen": {"n4096_cutoff2048": {"classical_equiv_qd_ops_per_s": 1.25e10}},
+              "durand_kerner": {"root_sweeps_per_s": 1.3e6}, "chebyshev_dk": {"single_solve_gpu_s": 0.33}}
+        rows = bench.cpu_baseline_rows(pool, ex)
+    finally:
+        pool.close()
+    assert set(rows) == set(ex)
+    for key, r in rows.items():
+        assert r["sample"] and r["gpu_over_oracle"] > 0, key
+    assert rows["axpy"]["gpu_elements_per_s"] == (1 << 24) / 3.2e-3
+    assert rows["chebyshev_dk"]["gpu_over_oracle"] == rows["chebyshev_dk"]["single_solve_s"] / 0.33
