@@ -18,7 +18,11 @@
  *   ddc : 2 x binary64, Algorithm 4 (DWAdd),     Algorithm 7 (DWMul)  -- the
  *         conventional double-double the paper benchmarks as "DD"
  *   td  : 3 x binary64, Algorithm 11 (TWBFAdd),  Algorithm 12 (TWBFMul)
+ *   tdc : 3 x binary64, Algorithm 9 (TWAdd),     Algorithm 10 (TWMul), each
+ *         ending in TWRenormalize -- the conventional triple-word arithmetic
  *   qd  : 4 x binary64, Algorithm 13 (QWBFAdd),  Algorithm 14 (QDBFMul)
+ *   qdc : 4 x binary64, the QD library's quad-word add and multiply, each
+ *         ending in QWRenormalize -- the conventional quad-word arithmetic
  *   ds  : 2 x binary32, Algorithms 6 / 8
  *   tf  : 3 x binary32, Algorithms 11 / 12
  *   qf  : 4 x binary32, Algorithms 13 / 14
@@ -77,6 +81,8 @@ static const prec_d P_dd = {2, dw_add_bf_d, dw_mul_bf_d, 2};
 static const prec_d P_ddc = {2, dw_add_sloppy_d, dw_mul_d, 2};
 static const prec_d P_td = {3, tw_add_bf_d, tw_mul_bf_d, 2};
 static const prec_d P_qd = {4, qw_add_bf_d, qw_mul_bf_d, 3};
+static const prec_d P_tdc = {3, tw_add_d, tw_mul_d, 2};
+static const prec_d P_qdc = {4, qw_add_d, qw_mul_d, 3};
 static const prec_f P_ds = {2, dw_add_bf_f, dw_mul_bf_f, 2};
 static const prec_f P_tf = {3, tw_add_bf_f, tw_mul_bf_f, 2};
 static const prec_f P_qf = {4, qw_add_bf_f, qw_mul_bf_f, 3};
@@ -183,6 +189,8 @@ MPREF_EXPORT_COMMON(dd, double, P_dd)
 MPREF_EXPORT_COMMON(ddc, double, P_ddc)
 MPREF_EXPORT_COMMON(td, double, P_td)
 MPREF_EXPORT_COMMON(qd, double, P_qd)
+MPREF_EXPORT_COMMON(tdc, double, P_tdc)
+MPREF_EXPORT_COMMON(qdc, double, P_qdc)
 #undef SFXV
 #define SFXV _f
 MPREF_EXPORT_COMMON(ds, float, P_ds)

@@ -32,6 +32,8 @@ PRECS = {
     "ddc": (2, np.float64),
     "td": (3, np.float64),
     "qd": (4, np.float64),
+    "tdc": (3, np.float64),
+    "qdc": (4, np.float64),
     "ds": (2, np.float32),
     "tf": (3, np.float32),
     "qf": (4, np.float32),
@@ -219,13 +221,17 @@ def recip(prec, a):
     return c
 
 
-def op_counts(prec, op):
-    """(add, sub, mul, fma) operation counts of one `op` ('add' or 'mul') in `prec`."""
+def op_counts(prec, op, a=None, b=None):
+    """(add, sub, mul, fma) operation counts of one `op` ('add' or 'mul') in `prec`,
+    summed over the elements of the K-arrays a and b (default: one element equal
+    to 1).  The branch-free algorithms count the same on every input; the
+    conventional ones (tdc, qdc) depend on their renormalisation's zero tests."""
     K, dt = PRECS[prec]
-    a = np.ones((K, 1), dtype=dt)
+    a = np.ones((K, 1), dtype=dt) if a is None else a
+    b = a if b is None else b
     L = lib(True)
     L.mpref_count_reset()
-    (add if op == "add" else mul)(prec, a, a, counting=True)
+    (add if op == "add" else mul)(prec, a, b, counting=True)
     out = np.zeros(4, dtype=np.int64)
     L.mpref_count_get(_p(out))
     return tuple(int(v) for v in out)

@@ -5,7 +5,9 @@ Each mutant edits one line of the oracle's C source: a wrong operand, TwoSum
 swapped for QuickTwoSum, a dropped term, a swapped component index, a sign
 slip, transposed GEMM indices, an off-by-one Horner coefficient, a Newton sign
 error, a Durand-Kerner product that includes j = i, a mis-wired Estrin tree, a
-Strassen product, combination or quadrant gone wrong.
+Strassen product, combination or quadrant gone wrong, a dropped term, wrong
+partner or component in the conventional triple- and quad-word algorithms or
+their renormalisation.
 The pin battery below
 (exact rationals, the op counts of Tables 1 and 2, error bounds, identities,
 permutation GEMM, known roots) must pass on the real oracle and fail on every
@@ -44,6 +46,17 @@ MUTANTS = [
     ("Alg6 dropped term", CORE, "g5 = ADD(g4, g3e);", "g5 = g4;"),
     ("Alg8 component index", CORE, "p10 = MUL(A[1], B[0]);", "p10 = MUL(A[1], B[1]);"),
     ("Alg4 dropped low sum", CORE, "REAL t = ADD(A[1], B[1]);\n    e = ADD(e, t);", "REAL t = ADD(A[1], B[1]);\n    e = ADD(e, 0 * t);"),
+    ("Alg9 dropped term", CORE, "t0 = ADD(ADD(t0, t1), t2);", "t0 = ADD(t0, t1);"),
+    ("Alg9 wrong partner", CORE, "F(two_sum)(t1, i1, &s2, &i3);", "F(two_sum)(t0, i1, &s2, &i3);"),
+    ("Alg10 component index", CORE, "x[4], o[4];\n    F(two_prod)(A[0], B[0], &p0, &q0);\n    F(two_prod)(A[0], B[1], &p1, &q1);\n    F(two_prod)(A[1], B[0], &p2, &q2);\n    F(two_prod)(A[0], B[2], &p3, &q3);\n    F(two_prod)(A[1], B[1], &p4, &q4);",
+     "x[4], o[4];\n    F(two_prod)(A[0], B[0], &p0, &q0);\n    F(two_prod)(A[0], B[1], &p1, &q1);\n    F(two_prod)(A[1], B[0], &p2, &q2);\n    F(two_prod)(A[0], B[2], &p3, &q3);\n    F(two_prod)(A[1], B[0], &p4, &q4);"),
+    ("Alg10 wrong renormalisation input", CORE, "x[0] = p0; x[1] = p1; x[2] = s0; x[3] = t0;\n    F(renorm)(x, 4, 4, o);",
+     "x[0] = p0; x[1] = p1; x[2] = p2; x[3] = t0;\n    F(renorm)(x, 4, 4, o);"),
+    ("QW add dropped term", CORE, "t[0] = ADD(ADD(t[0], t[1]), t[3]);", "t[0] = ADD(t[0], t[1]);"),
+    ("QW mul wrong eps^3 product", CORE, "F(two_prod)(A[3], B[0], &p9, &q9);", "F(two_prod)(A[3], B[1], &p9, &q9);"),
+    ("Renormalisation drops the last term", CORE, "r = ADD(r, t[i]);\n            continue;", "continue;"),
+    ("Renormalisation sweep operand order", CORE, "F(quick_two_sum)(x[i], s, &s, &t[i + 1]);",
+     "F(quick_two_sum)(s, x[i], &s, &t[i + 1]);"),
     ("TwoSum wrong operand", CORE, "REAL t3 = SUB(b, v);", "REAL t3 = SUB(b, s_);"),
     ("TwoProd sign", CORE, "*e = FMA(a, b, -p_);", "*e = FMA(a, b, p_);"),
     ("QuickTwoSum order", CORE, "REAL t = SUB(s_, a);\n    *e = SUB(b, t);", "REAL t = SUB(s_, b);\n    *e = SUB(a, t);"),
@@ -94,6 +107,13 @@ def _counts_and_eft(oracle, bad):
     check("op counts", oracle.op_counts("dd", "add") == (8, 12, 0, 0))
     check("op counts", oracle.op_counts("ddc", "add") == (5, 6, 0, 0))
     check("op counts", oracle.op_counts("dd", "mul") == (3, 2, 3, 1))
+    conv = g["conventional_rows"]
+    a, s, m, _, f = conv["TWxTW"]["counts"]
+    check("op counts", oracle.op_counts("tdc", "mul") == (a, s, m, f))
+    a, s, m, _, f = conv["TW+TW"]["counts"]
+    check("op counts", oracle.op_counts("tdc", "add") == (a + 2, s + 4, m, f))
+    check("op counts", oracle.op_counts("qdc", "add") == (30, 54, 0, 0))
+    check("op counts", oracle.op_counts("qdc", "mul") == (65, 94, 13, 10))
     # EFT exactness
     rng = np.random.default_rng(0)
     xs = rng.standard_normal(200) * np.exp2(rng.integers(-20, 20, 200))
@@ -118,7 +138,7 @@ def _check(bad):
 def _ops(oracle, bad):
     check = _check(bad)
     # per-op error bounds and identities
-    for prec in ("dd", "ddc", "td", "qd", "tf", "qf"):
+    for prec in ("dd", "ddc", "td", "qd", "tdc", "qdc", "tf", "qf"):
         K, dt = oracle.PRECS[prec]
         p = K * (53 if dt == np.float64 else 24)
         for name, a, b in families(oracle, prec, n=120, seed=5):
@@ -131,7 +151,7 @@ def _ops(oracle, bad):
                     if prec == "ddc" and op == "add":
                         check("sloppy add bound", abs(z - ex) <= Fraction(1, 2 ** 104) * (abs(x) + abs(y)))
                     else:
-                        lim = 2.0 ** -(p - 2) if op == "add" else 2.0 ** -(p - 4)
+                        lim = 2.0 ** -(p - 2) if op == "add" or prec in ("tdc", "qdc") else 2.0 ** -(p - 4)
                         check(f"{op} error bound", rel_err(z, ex) <= lim)
             check("commutativity", np.array_equal(oracle.add(prec, a, b), oracle.add(prec, b, a)))
             check("commutativity", np.array_equal(oracle.mul(prec, a, b), oracle.mul(prec, b, a)))

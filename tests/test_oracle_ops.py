@@ -21,7 +21,8 @@ from paper_2603_14926_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 BF_PRECS = ["dd", "td", "qd", "ds", "tf", "qf"]
-ALL_PRECS = ["dd", "ddc", "td", "qd", "ds", "tf", "qf"]
+ALL_PRECS = ["dd", "ddc", "td", "qd", "tdc", "qdc", "ds", "tf", "qf"]
+CONV_PRECS = ["tdc", "qdc"]
 
 
 def prec_bits(oracle, prec):
@@ -105,6 +106,132 @@ def test_op_counts_double_word(oracle):
     assert oracle.op_counts("ddc", "add") == (5, 6, 0, 0)
     assert oracle.op_counts("dd", "mul") == (3, 2, 3, 1)
     assert oracle.op_counts("ddc", "mul") == (3, 2, 3, 1)
+
+
+# ---------------------------------------------------------------------------
+# Conventional triple and quad word (Tables 1 and 2, the renormalising rows)
+# ---------------------------------------------------------------------------
+
+# building blocks as (add, sub, mul, fma): Algorithms 1-3 and the plain operations
+TS, QTS, TP, ADD_, MUL_ = (2, 4, 0, 0), (1, 2, 0, 0), (0, 0, 1, 1), (1, 0, 0, 0), (0, 0, 1, 0)
+
+
+def _blocks(**n):
+    parts = {"ts": TS, "qts": QTS, "tp": TP, "add": ADD_, "mul": MUL_}
+    return tuple(sum(n.get(k, 0) * v[i] for k, v in parts.items()) for i in range(4))
+
+
+def _typical(oracle, prec):
+    K, dt = oracle.PRECS[prec]
+    return (inputs.mp_uniform(0, 1, K, dt, stream=41), inputs.mp_uniform(0, 1, K, dt, stream=42))
+
+
+def test_conventional_tw_mul_counts_match_table1(oracle):
+    """Algorithm 10 (six TwoProds, sixteen TwoSums, five adds) plus TWRenormalize
+    (five QuickTwoSums on every path) gives Table 1's TWxTW row exactly, on a
+    typical input and on one whose lower components are zero."""
+    g = json.load(open(os.path.join(GOLDEN, "op_counts.json")))["conventional_rows"]
+    add, sub, mul, div, fma = g["TWxTW"]["counts"]
+    assert div == 0
+    assert _blocks(tp=6, ts=16, add=5, qts=5) == (add, sub, mul, fma)
+    assert oracle.op_counts("tdc", "mul") == (add, sub, mul, fma)
+    assert oracle.op_counts("tdc", "mul", *_typical(oracle, "tdc")) == (add, sub, mul, fma)
+
+
+def test_conventional_tw_add_counts_against_table1(oracle):
+    """Algorithm 9 as printed: three written-out TwoSums, four TwoSums, two adds,
+    then TWRenormalize (five QuickTwoSums, the count Table 1's TWxTW row fixes).
+    That is one TwoSum (2 adds, 4 subtractions) more than Table 1's TW+TW row,
+    which matches Algorithm 9 with its last TwoSum replaced by a plain add; the
+    algorithm is followed as printed."""
+    g = json.load(open(os.path.join(GOLDEN, "op_counts.json")))["conventional_rows"]
+    add, sub, mul, _, fma = g["TW+TW"]["counts"]
+    want = _blocks(ts=7, add=2, qts=5)
+    assert want == (add + 2, sub + 4, mul, fma)
+    assert oracle.op_counts("tdc", "add") == want
+    assert oracle.op_counts("tdc", "add", *_typical(oracle, "tdc")) == want
+
+
+def test_conventional_qw_counts(oracle):
+    """The QD library's quad-word add (ten TwoSums, three adds) and accurate
+    multiply (ten TwoProds, three products, twenty TwoSums, eighteen adds), each
+    with QWRenormalize: four QuickTwoSums, then three more, or two and an add
+    when every error term is nonzero (the typical path).  Table 2's QWxQW row
+    has the same 94 subtractions on the seven-QuickTwoSum path.  Its QW+QW row
+    (26 adds, 58 subtractions) cannot come from TwoSums, QuickTwoSums and plain
+    adds at all, since each of these has at most twice as many subtractions as
+    additions."""
+    g = json.load(open(os.path.join(GOLDEN, "op_counts.json")))["conventional_rows"]
+    assert oracle.op_counts("qdc", "add") == _blocks(ts=10, add=3, qts=7)
+    assert oracle.op_counts("qdc", "add", *_typical(oracle, "qdc")) == _blocks(ts=10, add=4, qts=6)
+    assert oracle.op_counts("qdc", "mul") == _blocks(tp=10, mul=3, ts=20, add=18, qts=7)
+    assert oracle.op_counts("qdc", "mul", *_typical(oracle, "qdc")) == _blocks(tp=10, mul=3, ts=20, add=19,
+                                                                               qts=6)
+    assert oracle.op_counts("qdc", "mul")[1] == g["QWxQW"]["counts"][1]
+    add, sub = g["QW+QW"]["counts"][:2]
+    assert sub > 2 * add
+
+
+@pytest.mark.parametrize("prec", CONV_PRECS)
+@pytest.mark.parametrize("op", ["add", "mul"])
+def test_conventional_error_bound(oracle, prec, op):
+    """The renormalising algorithms keep the same adopted bounds as the
+    branch-free ones (2^-(p-2) relative for add and 2^-(p-4) for multiply); the
+    accurate multiply keeps every term down to order eps^4 and is held to
+    2^-(p-2).  Observed: add 2^-(p+2), multiply 2^-(p+0.6) (TD) and 2^-(p+3) (QD)."""
+    p = prec_bits(oracle, prec)
+    bound = 2.0 ** -(p - 2)
+    worst = 0.0
+    for name, a, b in families(oracle, prec):
+        c = getattr(oracle, op)(prec, a, b)
+        for x, y, z in zip(mp_values(a), mp_values(b), mp_values(c)):
+            e = rel_err(z, x + y if op == "add" else x * y)
+            worst = max(worst, e)
+            assert e <= bound, (name, prec, op, e)
+    assert worst > 0
+
+
+@pytest.mark.parametrize("prec", CONV_PRECS)
+def test_conventional_agrees_with_branch_free(oracle, prec):
+    """Both families approximate the same exact result: conventional and
+    branch-free sums and products differ by no more than their two bounds."""
+    bf = prec[:-1]
+    p = prec_bits(oracle, prec)
+    for name, a, b in families(oracle, prec, n=300, seed=3):
+        for op in ("add", "mul"):
+            c1 = mp_values(getattr(oracle, op)(prec, a, b))
+            c2 = mp_values(getattr(oracle, op)(bf, a, b))
+            for x, y in zip(c1, c2):
+                assert abs(x - y) <= Fraction(2) ** -(p - 5) * max(abs(x), abs(y)), (name, op)
+
+
+def test_renormalisation_compacts_exact_sums(oracle):
+    """Sums whose exact value needs fewer components than K come out with the
+    zeros last (the zero tests of the renormalisation): 1 + 2^-k in QD, and
+    products of two one-component numbers, which TwoProd makes exact."""
+    K = 4
+    for k in (1, 30, 60, 110, 170):
+        a = np.zeros((K, 1))
+        b = np.zeros((K, 1))
+        a[0, 0] = 1.0
+        b[0, 0] = 2.0 ** -k
+        for prec in ("qdc", "tdc"):
+            Kp = oracle.PRECS[prec][0]
+            c = oracle.add(prec, a[:Kp], b[:Kp])
+            assert mp_value(c[:, 0]) == 1 + Fraction(2) ** -k
+            nz = [float(v) != 0 for v in c[:, 0]]
+            assert nz == sorted(nz, reverse=True), (prec, k, c[:, 0])
+    rng = np.random.default_rng(4)
+    for prec in CONV_PRECS:
+        Kp = oracle.PRECS[prec][0]
+        a = np.zeros((Kp, 50))
+        b = np.zeros((Kp, 50))
+        a[0] = rng.standard_normal(50)
+        b[0] = rng.standard_normal(50)
+        c = oracle.mul(prec, a, b)
+        for i in range(50):
+            assert mp_value(c[:, i]) == Fraction(float(a[0, i])) * Fraction(float(b[0, i]))
+            assert not c[2:, i].any()
 
 
 # ---------------------------------------------------------------------------
