@@ -17,12 +17,22 @@
  *         -- the conventional double-double the paper benchmarks as "DD"
  *   td  : 3 x binary64, Algorithms 11 (TWBFAdd) and 12 (TWBFMul)
  *   qd  : 4 x binary64, Algorithms 13 (QWBFAdd) and 14 (QDBFMul)
+ *   tdc : 3 x binary64, Algorithms 9 (TWAdd) and 10 (TWMul), each ending in
+ *         TWRenormalize -- the conventional triple word of Table 4's
+ *         standard / BF ratio; Algorithm 10's last TwoSum, printed with q3,
+ *         is read with the order-eps^3 sum t0
+ *   qdc : 4 x binary64, the QD library's quad-word add (sloppy form) and
+ *         multiply (accurate form), each ending in QWRenormalize -- the
+ *         conventional quad word (Section 2.3 names these without printing
+ *         them; they follow Hida, Li and Bailey, ARITH-15, 2001)
  *   ds  : 2 x binary32, Algorithms 6 and 8
  *   tf  : 3 x binary32, Algorithms 11 and 12
  *   qf  : 4 x binary32, Algorithms 13 and 14
- * T below is double for dd/ddc/td/qd and float for ds/tf/qf; K is the number of
- * components.  Root solving and polynomial construction exist for the binary64
- * precisions only.
+ * T below is double for dd/ddc/td/qd/tdc/qdc and float for ds/tf/qf; K is the
+ * number of components.  Root solving and polynomial construction exist for
+ * dd/ddc/td/qd only.  tdc and qdc provide the elementwise, AXPY, dot, GEMV,
+ * GEMM and Strassen families (their renormalisations branch on zero tests;
+ * results are still bit-identical to the CPU oracle).
  *
  * LAYOUT.  A "K-array" of n numbers is K planes of n components each: component
  * c (0 = leading) of element i is at ptr[c * plane_stride + i].  Plane strides
@@ -374,6 +384,15 @@ MPGPU_DECL_ALL(dd, double)
 MPGPU_DECL_ALL(ddc, double)
 MPGPU_DECL_ALL(td, double)
 MPGPU_DECL_ALL(qd, double)
+#define MPGPU_DECL_CONVENTIONAL(P, T)                                                       \
+    MPGPU_DECL_EW(P, T)                                                                     \
+    MPGPU_DECL_AXPY(P, T)                                                                   \
+    MPGPU_DECL_DOT(P, T)                                                                    \
+    MPGPU_DECL_GEMV(P, T)                                                                   \
+    MPGPU_DECL_GEMM(P, T)                                                                   \
+    MPGPU_DECL_STRASSEN(P, T)
+MPGPU_DECL_CONVENTIONAL(tdc, double)
+MPGPU_DECL_CONVENTIONAL(qdc, double)
 MPGPU_DECL_ALL(ds, float)
 MPGPU_DECL_ALL(tf, float)
 MPGPU_DECL_ALL(qf, float)

@@ -7,7 +7,7 @@ runs in the library's CUDA kernels; there is no fallback.  PyTorch provides the
 device memory and streams.
 
 Numbers are "K-arrays": torch tensors of shape (K, ...) on a CUDA device,
-float64 for dd/ddc/td/qd and float32 for ds/tf/qf, each component plane
+float64 for dd/ddc/td/qd/tdc/qdc and float32 for ds/tf/qf, each component plane
 contiguous (component 0 leading).  Complex K-arrays have 2K planes.
 """
 
@@ -18,8 +18,11 @@ import os
 import threading
 
 PRECS = {"dd": (2, "float64"), "ddc": (2, "float64"), "td": (3, "float64"),
-         "qd": (4, "float64"), "ds": (2, "float32"), "tf": (3, "float32"),
-         "qf": (4, "float32")}
+         "qd": (4, "float64"), "tdc": (3, "float64"), "qdc": (4, "float64"),
+         "ds": (2, "float32"), "tf": (3, "float32"), "qf": (4, "float32")}
+# conventional (renormalising) precisions: elementwise, BLAS-1, GEMV, GEMM and
+# Strassen families only
+CONVENTIONAL = ("tdc", "qdc")
 DK_PRECS = ("dd", "ddc", "td", "qd")
 # per-polynomial solver status codes (mp_roots_P)
 DK_CAP, DK_CONVERGED, DK_STAGNATED, DK_TIMEOUT, DK_BREAKDOWN = 0, 1, 2, 3, 4
@@ -87,10 +90,11 @@ def _declare(L):
             f.restype = _int
         getattr(L, f"mp_dot_workspace_{p}").argtypes = [_i64]
         getattr(L, f"mp_dot_workspace_{p}").restype = ctypes.c_size_t
-        getattr(L, f"mp_polyeval_backward_workspace_{p}").argtypes = [_i64, _i64]
-        getattr(L, f"mp_polyeval_backward_workspace_{p}").restype = ctypes.c_size_t
-        getattr(L, f"mp_cgemm_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
-        getattr(L, f"mp_cgemm_workspace_{p}").restype = ctypes.c_size_t
+        if p not in CONVENTIONAL:
+            getattr(L, f"mp_polyeval_backward_workspace_{p}").argtypes = [_i64, _i64]
+            getattr(L, f"mp_polyeval_backward_workspace_{p}").restype = ctypes.c_size_t
+            getattr(L, f"mp_cgemm_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
+            getattr(L, f"mp_cgemm_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_strassen_workspace_{p}").argtypes = [_i64, _i64, _i64, _i64]
         getattr(L, f"mp_gemm_strassen_workspace_{p}").restype = ctypes.c_size_t
         getattr(L, f"mp_gemm_num_configs_{p}").restype = _int

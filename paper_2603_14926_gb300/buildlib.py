@@ -27,7 +27,7 @@ LIB = os.path.join(LIBDIR, "libmpgpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fno-fast-math", f"-I{INCLUDE}", f"-I{CSRC}"]
-GEMM_PRECS = ("dd", "ddc", "td", "qd", "ds", "tf", "qf")
+GEMM_PRECS = ("dd", "ddc", "td", "qd", "tdc", "qdc", "ds", "tf", "qf")
 
 
 def nvcc() -> str:

@@ -532,6 +532,8 @@ MP_EXPORT_BLAS1(dd, P_dd)
 MP_EXPORT_BLAS1(ddc, P_ddc)
 MP_EXPORT_BLAS1(td, P_td)
 MP_EXPORT_BLAS1(qd, P_qd)
+MP_EXPORT_BLAS1(tdc, P_tdc)
+MP_EXPORT_BLAS1(qdc, P_qdc)
 MP_EXPORT_BLAS1(ds, P_ds)
 MP_EXPORT_BLAS1(tf, P_tf)
 MP_EXPORT_BLAS1(qf, P_qf)

@@ -535,7 +535,7 @@ using namespace mp;
     extern "C" const char *mp_gemm_config_name_##S(int c) { return GemmTable<PT>::name(c); }
 
 #ifndef MPGPU_GEMM_PREC
-#error "compile k_gemm.cu with -DMPGPU_GEMM_PREC=<dd|ddc|td|qd|ds|tf|qf>"
+#error "compile k_gemm.cu with -DMPGPU_GEMM_PREC=<dd|ddc|td|qd|tdc|qdc|ds|tf|qf>"
 #endif
 #define MP_CAT2(a, b) a##b
 #define MP_CAT(a, b) MP_CAT2(a, b)

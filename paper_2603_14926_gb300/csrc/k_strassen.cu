@@ -35,6 +35,8 @@ MP_STRASSEN_LEAF(P_dd, mp_gemm_ex_dd)
 MP_STRASSEN_LEAF(P_ddc, mp_gemm_ex_ddc)
 MP_STRASSEN_LEAF(P_td, mp_gemm_ex_td)
 MP_STRASSEN_LEAF(P_qd, mp_gemm_ex_qd)
+MP_STRASSEN_LEAF(P_tdc, mp_gemm_ex_tdc)
+MP_STRASSEN_LEAF(P_qdc, mp_gemm_ex_qdc)
 MP_STRASSEN_LEAF(P_ds, mp_gemm_ex_ds)
 MP_STRASSEN_LEAF(P_tf, mp_gemm_ex_tf)
 MP_STRASSEN_LEAF(P_qf, mp_gemm_ex_qf)
@@ -235,6 +237,8 @@ MP_EXPORT_STRASSEN(dd, P_dd)
 MP_EXPORT_STRASSEN(ddc, P_ddc)
 MP_EXPORT_STRASSEN(td, P_td)
 MP_EXPORT_STRASSEN(qd, P_qd)
+MP_EXPORT_STRASSEN(tdc, P_tdc)
+MP_EXPORT_STRASSEN(qdc, P_qdc)
 MP_EXPORT_STRASSEN(ds, P_ds)
 MP_EXPORT_STRASSEN(tf, P_tf)
 MP_EXPORT_STRASSEN(qf, P_qf)

@@ -4,6 +4,8 @@
 //   Algorithms 1-3  (QuickTwoSum, TwoSum, FMA TwoProd)
 //   Algorithms 4, 6 (DWAdd sloppy, DWBFAdd), 7, 8 (DWMul, DWBFMul)
 //   Algorithms 11, 12 (TWBFAdd, TWBFMul), 13, 14 (QWBFAdd, QDBFMul)
+//   Algorithms 9, 10 (TWAdd, TWMul) and the QD library's quad-word add and
+//   multiply, with their renormalisations (the conventional baseline)
 // on binary64 (FP64 pipe) or binary32 (FP32 pipe) components.
 //
 // Every floating-point step is an explicit round-to-nearest-even intrinsic
@@ -337,6 +339,224 @@ __device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 
 }
 
 // ---------------------------------------------------------------------------
+// Conventional (renormalising) triple and quad word: the "standard" side of
+// Table 4.  TWAdd / TWMul are Algorithms 9 / 10; the renormalisations and the
+// quad-word add / multiply, which the paper names but does not print, follow
+// the QD library's published description (Hida, Li and Bailey, ARITH-15,
+// 2001).  Their zero tests are real branches here: the point of this baseline
+// is the data-dependent control flow that the branch-free algorithms remove.
+// A zero test looks at the bit pattern (+0 and -0 are zero), which decides
+// exactly like an IEEE compare but issues on the integer pipe.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
+
+// TWRenormalize of (x0, x1, x2, x3): a bottom-up sweep of QuickTwoSums, then a
+// top-down one that opens a new component wherever an error term is nonzero
+// (always five QuickTwoSums); the first three of the four components are kept.
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 3> tw_renorm(T x0, T x1, T x2, T x3, E &g)
+{
+    T s, t0, t1, t2, t3;
+    g.quick_two_sum(x2, x3, s, t3);
+    g.quick_two_sum(x1, s, s, t2);
+    g.quick_two_sum(x0, s, t0, t1);
+    T s0 = t0, s1 = t1, s2 = T(0), s3;
+    if (nonzero(t1)) {
+        g.quick_two_sum(s1, t2, s1, s2);
+        if (nonzero(s2))
+            g.quick_two_sum(s2, t3, s2, s3);
+        else
+            g.quick_two_sum(s1, t3, s1, s2);
+    } else {
+        g.quick_two_sum(s0, t2, s0, s1);
+        if (nonzero(s1))
+            g.quick_two_sum(s1, t3, s1, s2);
+        else
+            g.quick_two_sum(s0, t3, s0, s1);
+    }
+    mpv<T, 3> r;
+    r.c[0] = s0;
+    r.c[1] = s1;
+    r.c[2] = s2;
+    return r;
+}
+
+// QWRenormalize of (x0, ..., x4): the same two sweeps into four components; once
+// only the last component is still open, the remaining term is added into it.
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 4> qw_renorm(T x0, T x1, T x2, T x3, T x4, E &g)
+{
+    T s, t0, t1, t2, t3, t4;
+    g.quick_two_sum(x3, x4, s, t4);
+    g.quick_two_sum(x2, s, s, t3);
+    g.quick_two_sum(x1, s, s, t2);
+    g.quick_two_sum(x0, s, t0, t1);
+    T s0 = t0, s1 = t1, s2 = T(0), s3 = T(0);
+    if (nonzero(t1)) {
+        g.quick_two_sum(s1, t2, s1, s2);
+        if (nonzero(s2)) {
+            g.quick_two_sum(s2, t3, s2, s3);
+            if (nonzero(s3))
+                s3 = g.add(s3, t4);
+            else
+                g.quick_two_sum(s2, t4, s2, s3);
+        } else {
+            g.quick_two_sum(s1, t3, s1, s2);
+            if (nonzero(s2))
+                g.quick_two_sum(s2, t4, s2, s3);
+            else
+                g.quick_two_sum(s1, t4, s1, s2);
+        }
+    } else {
+        g.quick_two_sum(s0, t2, s0, s1);
+        if (nonzero(s1)) {
+            g.quick_two_sum(s1, t3, s1, s2);
+            if (nonzero(s2))
+                g.quick_two_sum(s2, t4, s2, s3);
+            else
+                g.quick_two_sum(s1, t4, s1, s2);
+        } else {
+            g.quick_two_sum(s0, t3, s0, s1);
+            if (nonzero(s1))
+                g.quick_two_sum(s1, t4, s1, s2);
+            else
+                g.quick_two_sum(s0, t4, s0, s1);
+        }
+    }
+    mpv<T, 4> r;
+    r.c[0] = s0;
+    r.c[1] = s1;
+    r.c[2] = s2;
+    r.c[3] = s3;
+    return r;
+}
+
+// Algorithm 9 (TWAdd).  The three component-wise sums and their errors are the
+// written-out form of three TwoSums (Algorithm 2's operation sequence).
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 3> tw_add_conv(const mpv<T, 3> &A, const mpv<T, 3> &B, E &g)
+{
+    T s0, s1, s2, t0, t1, t2, i1, i2, i3;
+    g.two_sum(A.c[0], B.c[0], s0, t0);
+    g.two_sum(A.c[1], B.c[1], s1, t1);
+    g.two_sum(A.c[2], B.c[2], s2, t2);
+    g.two_sum(s1, t0, s1, t0);
+    g.two_sum(s2, t0, i1, i2);
+    g.two_sum(t1, i1, s2, i3);
+    g.two_sum(i2, i3, t0, t1);
+    t0 = g.add(g.add(t0, t1), t2);
+    return tw_renorm<T>(s0, s1, s2, t0, g);
+}
+
+// (a, b, c) -> (a + b + c, error, error) by three TwoSums (the QD library's three-sum).
+template <typename T, class E> __device__ __forceinline__ void three_sum(T &a, T &b, T &c, E &g)
+{
+    T i1, i2, i3;
+    g.two_sum(a, b, i1, i2);
+    g.two_sum(c, i1, a, i3);
+    g.two_sum(i2, i3, b, c);
+}
+
+// Algorithm 10 (TWMul); its final "TwoSum(q3, s1)" is read as TwoSum(t0, s1),
+// the order-eps^3 sum t0 plus s1.  The unused s2 and final t1 are not formed.
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 3> tw_mul_conv(const mpv<T, 3> &A, const mpv<T, 3> &B, E &g)
+{
+    T p0, q0, p1, q1, p2, q2, p3, q3, p4, q4, p5, q5, s0, s1, t0, t1;
+    g.two_prod(A.c[0], B.c[0], p0, q0);
+    g.two_prod(A.c[0], B.c[1], p1, q1);
+    g.two_prod(A.c[1], B.c[0], p2, q2);
+    g.two_prod(A.c[0], B.c[2], p3, q3);
+    g.two_prod(A.c[1], B.c[1], p4, q4);
+    g.two_prod(A.c[2], B.c[0], p5, q5);
+    three_sum<T>(p1, p2, q0, g);
+    three_sum<T>(p2, q1, q2, g);
+    three_sum<T>(p3, p4, p5, g);
+    g.two_sum(p2, p3, s0, t0);
+    g.two_sum(q1, p4, s1, t1);
+    g.two_sum(s1, t0, s1, t0);
+    g.two_sum(q0, q3, q0, q3);
+    g.two_sum(q4, q5, q4, q5);
+    T u;
+    g.two_sum(q0, q4, t0, u);
+    g.two_sum(t0, s1, t0, t1);
+    return tw_renorm<T>(p0, p1, s0, t0, g);
+}
+
+// The QD library's quad-word add ("sloppy"): component-wise TwoSums, the errors
+// folded in by a TwoSum, a three-sum and a three-sum with a plain add for its
+// error, then QWRenormalize(s0, s1, s2, s3, t0).
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 4> qw_add_conv(const mpv<T, 4> &A, const mpv<T, 4> &B, E &g)
+{
+    T s0, s1, s2, s3, t0, t1, t2, t3, i1, i2, i3;
+    g.two_sum(A.c[0], B.c[0], s0, t0);
+    g.two_sum(A.c[1], B.c[1], s1, t1);
+    g.two_sum(A.c[2], B.c[2], s2, t2);
+    g.two_sum(A.c[3], B.c[3], s3, t3);
+    g.two_sum(s1, t0, s1, t0);
+    three_sum<T>(s2, t0, t1, g);
+    g.two_sum(s3, t0, i1, i2);
+    g.two_sum(t2, i1, s3, i3);
+    t0 = g.add(i2, i3);
+    t0 = g.add(g.add(t0, t1), t3);
+    return qw_renorm<T>(s0, s1, s2, s3, t0, g);
+}
+
+// The QD library's quad-word multiply (accurate form): Algorithm 10's steps
+// through the order-eps^2 terms; the order-eps^3 terms (errors q0, q3, q4, q5,
+// products a0b3, a1b2, a2b1, a3b0, and s1) summed as double words; the
+// order-eps^4 terms (a1b3, a2b2, a3b1, errors q6..q9, s2) added left to right
+// into the low word; then QWRenormalize(p0, p1, s0, t0, t1).
+template <typename T, class E>
+__device__ __forceinline__ mpv<T, 4> qw_mul_conv(const mpv<T, 4> &A, const mpv<T, 4> &B, E &g)
+{
+    T p0, q0, p1, q1, p2, q2, p3, q3, p4, q4, p5, q5, p6, q6, p7, q7, p8, q8, p9, q9;
+    T s0, s1, s2, t0, t1, r0, r1;
+    g.two_prod(A.c[0], B.c[0], p0, q0);
+    g.two_prod(A.c[0], B.c[1], p1, q1);
+    g.two_prod(A.c[1], B.c[0], p2, q2);
+    g.two_prod(A.c[0], B.c[2], p3, q3);
+    g.two_prod(A.c[1], B.c[1], p4, q4);
+    g.two_prod(A.c[2], B.c[0], p5, q5);
+    three_sum<T>(p1, p2, q0, g);
+    three_sum<T>(p2, q1, q2, g);
+    three_sum<T>(p3, p4, p5, g);
+    g.two_sum(p2, p3, s0, t0);
+    g.two_sum(q1, p4, s1, t1);
+    s2 = g.add(q2, p5);
+    g.two_sum(s1, t0, s1, t0);
+    s2 = g.add(s2, g.add(t0, t1));
+    g.two_prod(A.c[0], B.c[3], p6, q6);
+    g.two_prod(A.c[1], B.c[2], p7, q7);
+    g.two_prod(A.c[2], B.c[1], p8, q8);
+    g.two_prod(A.c[3], B.c[0], p9, q9);
+    g.two_sum(q0, q3, q0, q3);
+    g.two_sum(q4, q5, q4, q5);
+    g.two_sum(p6, p7, p6, p7);
+    g.two_sum(p8, p9, p8, p9);
+    g.two_sum(q0, q4, t0, t1);
+    t1 = g.add(t1, g.add(q3, q5));
+    g.two_sum(p6, p8, r0, r1);
+    r1 = g.add(r1, g.add(p7, p9));
+    g.two_sum(t0, r0, q3, q4);
+    q4 = g.add(q4, g.add(t1, r1));
+    g.two_sum(q3, s1, t0, t1);
+    t1 = g.add(t1, q4);
+    T u = g.add(g.mul(A.c[1], B.c[3]), g.mul(A.c[2], B.c[2]));
+    u = g.add(u, g.mul(A.c[3], B.c[1]));
+    u = g.add(u, q6);
+    u = g.add(u, q7);
+    u = g.add(u, q8);
+    u = g.add(u, q9);
+    u = g.add(u, s2);
+    t1 = g.add(t1, u);
+    return qw_renorm<T>(p0, p1, s0, t0, t1, g);
+}
+
+// ---------------------------------------------------------------------------
 // Precision tags: component type, K, add, multiply, reciprocal Newton steps.
 // ---------------------------------------------------------------------------
 
@@ -371,6 +591,8 @@ MP_PREC_TAG(P_dd, double, 2, dw_add_bf<double>, dw_mul_bf<double>, 2, true)
 MP_PREC_TAG(P_ddc, double, 2, dw_add_sloppy<double>, dw_mul_bf<double>, 2, true)
 MP_PREC_TAG(P_td, double, 3, tw_add_bf<double>, tw_mul_bf<double>, 2, true)
 MP_PREC_TAG(P_qd, double, 4, qw_add_bf<double>, qw_mul_bf<double>, 3, true)
+MP_PREC_TAG(P_tdc, double, 3, tw_add_conv<double>, tw_mul_conv<double>, 2, true)
+MP_PREC_TAG(P_qdc, double, 4, qw_add_conv<double>, qw_mul_conv<double>, 3, true)
 MP_PREC_TAG(P_ds, float, 2, dw_add_bf<float>, dw_mul_bf<float>, 2, false)
 MP_PREC_TAG(P_tf, float, 3, tw_add_bf<float>, tw_mul_bf<float>, 2, false)
 MP_PREC_TAG(P_qf, float, 4, qw_add_bf<float>, qw_mul_bf<float>, 3, false)
