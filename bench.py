@@ -591,6 +591,108 @@ def extras(prec="qd", quick=False):
             **rates(macs * ins + sums * add_instr(prec), macs * ins_paper + sums * INSTR_ADD[prec], t2)}
         del A2, B2, C2, ws2
     out["gemm_strassen"] = strassen
+    out["bf_over_nobf"] = bf_over_nobf_extra((1024,) if quick else (1024, 2048))
+    out["eq1_n2049"] = eq1_extra(1025 if quick else 2049)
+    return out
+
+
+def bf_over_nobf_extra(sizes):
+    """Table 4's standard / BF ratio in its GPU form: the same square GEMM kernel
+    and engine with the conventional arithmetic (ddc: Algorithms 4 + 7; tdc:
+    Algorithms 9 + 10 with TWRenormalize; qdc: the QD library's quad word with
+    QWRenormalize) over the branch-free one (dd, td, qd: Algorithms 6/8, 11/12,
+    13/14).  Both engines: the hybrid one (built-in, TwoSum's error term on the
+    integer pipes) and the all-FP64 one (configuration 4)."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    out = {}
+    for bf, nb in (("dd", "ddc"), ("td", "tdc"), ("qd", "qdc")):
+        K = mpg.PRECS[bf][0]
+        row = {}
+        for n in sizes:
+            A = dev(inputs.mp_uniform(2, (n, n), K, stream=inputs.STREAM_A))
+            B = dev(inputs.mp_uniform(2, (n, n), K, stream=inputs.STREAM_B))
+            C = mpg.empty(bf, n, n)
+            for cfg, eng in ((-1, "hybrid"), (4, "fp64")):
+                ms = {}
+                for p in (bf, nb):
+                    mpg.gemm(p, A, B, out=C, config=cfg)  # warm (module load, first launch)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    mpg.gemm(p, A, B, out=C, config=cfg)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms[p] = e0.elapsed_time(e1)
+                row[f"n{n}_{eng}"] = {f"{bf}_ms": ms[bf], f"{nb}_ms": ms[nb], "standard_over_bf": ms[nb] / ms[bf]}
+            del A, B, C
+        out[bf.upper()] = row
+    out["paper_table4"] = {"Snapdragon": {"DD": [0.6, 0.7], "TD": [1.2, 1.4], "QD": [2.0, 1.4]},
+                           "EPYC": {"DD": [1.0, 0.7], "TD": [1.4, 1.5], "QD": [1.5, 1.9]},
+                           "columns": "nonSIMD, SIMD (Strassen GEMM, averaged over n)"}
+    return out
+
+
+def eq1_extra(n):
+    """Section 3.1's real GEMM on its own matrices (Eq. 1) at Table 3's n = 2049:
+    classical fold and Strassen's recursion (one level: leaves of 1025; two
+    levels: leaves of 513), seconds and correct decimal digits against the exact
+    product c_ij = sqrt15 * S_i, over every row and the first and last columns."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    from fractions import Fraction
+
+    s15 = inputs.sqrt_fraction(15)
+    S = inputs.eq1_row_sums(n)
+    out = {"n": n}
+    for prec in ("dd", "td", "qd"):
+        K = mpg.PRECS[prec][0]
+        s5, s3, t, ia, ib = inputs.eq1_factors(n, K)
+        r5 = mpg.mul(prec, dev(np.repeat(s5[:, None], 2 * n, 1)), dev(t))
+        r3 = mpg.mul(prec, dev(np.repeat(s3[:, None], 2 * n, 1)), dev(t))
+        A = r5[:, torch.from_numpy(ia).cuda()].contiguous()
+        B = r3[:, torch.from_numpy(ib).cuda()].contiguous()
+        del r5, r3
+        row = {}
+        for name, cut in (("classical", None), ("strassen_1_level", (n + 1) // 2 + 1),
+                          ("strassen_2_levels", (n + 3) // 4 + 1)):
+            C = mpg.empty(prec, n, n)
+            ws = None
+            if cut is not None:
+                ws = torch.empty(max(mpg.gemm_strassen_workspace(prec, n, n, n, cut), 1), dtype=torch.uint8,
+                                 device="cuda")
+            run = (lambda: mpg.gemm(prec, A, B, out=C)) if cut is None else \
+                (lambda: mpg.gemm_strassen(prec, A, B, cut, out=C, ws=ws))
+            run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            h = C[:, :, [0, n - 1]].cpu().numpy()
+            worst = math.inf
+            for i in range(n):
+                ex = s15 * S[i]
+                for c in range(2):
+                    got = sum((Fraction(float(v)) for v in h[:, i, c]), Fraction(0))
+                    worst = min(worst, -math.log10(float(abs(got - ex) / ex)))
+            row[name] = {"s": e0.elapsed_time(e1) / 1e3, "digits": worst,
+                         **({"cutoff": cut} if cut is not None else {})}
+            del C, ws
+        out[prec] = row
+        del A, B
+    out["paper_section_3_1_digits"] = {"dd": [29.0, 30.4], "td": [45.5, 47.5], "qd": [61.7, 63.5]}
+    out["paper_table3_s_n2049"] = {"EPYC 32 threads, block": {"dd": 0.9, "td": 3.4, "qd": 6.2},
+                                   "EPYC 1 thread, BF Strassen + AVX2": {"dd": 10.3, "td": 30.4, "qd": 59.9}}
     return out
 
 

@@ -255,3 +255,41 @@ def horner_points(seed: int, npoly: int, npts: int) -> np.ndarray:
     """Real evaluation points uniform in [-1, 1): shape (npoly, npts), binary64."""
     base = (int(seed) * 0x100000001B3 + STREAM_X) & 0xFFFFFFFFFFFFFFFF
     return uniform_pm1(base, npoly * npts, 0).reshape(npoly, npts)
+
+
+def sqrt_fraction(v: int, bits: int = 400):
+    """sqrt(v) truncated to `bits` fractional bits, as an exact Fraction (integer
+    square root; no floating point)."""
+    import math
+    from fractions import Fraction
+
+    return Fraction(math.isqrt(int(v) << (2 * bits)), 1 << bits)
+
+
+def eq1_factors(n: int, K: int, dtype=np.float64):
+    """Factors of the real GEMM test matrices of Section 3.1 (Eq. 1),
+    a_ij = sqrt5 (i + j - 1) and b_ij = sqrt3 (n - i + 1), i, j = 1..n.
+
+    Returns (s5, s3, t, ia, ib): s5 and s3 are the greedy K-component expansions
+    of sqrt5 and sqrt3 (shape (K,)), t the integers 0..2n-1 as a K-array (shape
+    (K, 2n)), ia and ib (n, n) index maps with ia[i-1, j-1] = i + j - 1 and
+    ib[i-1, j-1] = n - i + 1.  Callers form r5 = s5 * t and r3 = s3 * t with
+    their own K-component multiply (the one step of multicomponent arithmetic)
+    and gather A = r5[:, ia], B = r3[:, ib]."""
+    s5 = rational_to_mp([sqrt_fraction(5)], K, dtype)[:, 0]
+    s3 = rational_to_mp([sqrt_fraction(3)], K, dtype)[:, 0]
+    t = np.zeros((K, 2 * n), dtype=dtype)
+    t[0] = np.arange(2 * n)
+    i = np.arange(1, n + 1)[:, None]
+    j = np.arange(1, n + 1)[None, :]
+    ia = (i + j - 1).astype(np.int64)
+    ib = np.broadcast_to(n - i + 1, (n, n)).astype(np.int64)
+    return s5, s3, t, ia, ib
+
+
+def eq1_row_sums(n: int) -> list:
+    """S_i = sum_{k=1..n} (i + k - 1)(n - k + 1) for i = 1..n, exact integers: the
+    exact product of Eq. 1's matrices is c_ij = sqrt15 * S_i (independent of j)."""
+    base = sum(k * (n - k + 1) for k in range(1, n + 1))  # i = 1
+    w = n * (n + 1) // 2                                  # sum_k (n - k + 1)
+    return [base + (i - 1) * w for i in range(1, n + 1)]

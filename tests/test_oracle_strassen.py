@@ -107,3 +107,22 @@ def test_strassen_eq1_accuracy_digits(oracle, prec, n):
             digits = min(digits, -math.log10(float(abs(mp_value(C[:, i - 1, j - 1]) - ex) / ex)))
     assert digits >= lo, digits
     assert digits <= K * 53 * math.log10(2) + 1.5, digits
+
+
+@pytest.mark.parametrize("prec", ["dd", "td", "qd", "qdc"])
+@pytest.mark.parametrize("shape", [(65, 65, 65), (70, 67, 69), (64, 66, 65)])
+def test_one_level_entry_helper_matches_recursion(oracle, prec, shape):
+    """The entry-at-a-time form of one Strassen level (tests/cases.py), used to
+    check full-size GPU products one entry at a time, equals the oracle's
+    recursion bit for bit in every quadrant, odd and even sizes."""
+    from cases import strassen_one_level_entry
+
+    m, n, k = shape
+    K, dt = oracle.PRECS[prec]
+    A = inputs.mp_uniform(31, (m, k), K, dt)
+    B = inputs.mp_uniform(32, (k, n), K, dt)
+    cutoff = min(shape)  # one level: the halves drop below it
+    C = oracle.gemm_strassen(prec, A, B, cutoff)
+    for i, j in [(0, 0), (0, n - 1), (m - 1, 0), (m - 1, n - 1), (m // 2, n // 2), (3, 40), (40, 3)]:
+        got = strassen_one_level_entry(oracle, prec, A, B, i, j)
+        assert np.array_equal(got.view(np.uint64), C[:, i, j].view(np.uint64)), (i, j)
