@@ -278,9 +278,11 @@ const char *mp_version(void);
 /* npoly * npts <= MP_NOALLOC_MAX_POINTS (131072 points); larger ones return  */
 /* MP_ENOMEM before anything is enqueued (dx-only calls have no limit).  The   */
 /* first call on a device looks the array up (cudaGetSymbolAddress) for that  */
-/* device, so make it before any stream capture.  Calls share the array:      */
-/* calls whose kernels overlap on the GPU race on it.  It needs no            */
-/* initialisation between calls.                                              */
+/* device, so make it before any stream capture.  Concurrent calls from host */
+/* threads are safe on the host side (the lookup is guarded), but calls share */
+/* the array: calls whose kernels overlap on the GPU race on it.  It needs no */
+/* initialisation between calls.  After cudaDeviceReset on a device, do not  */
+/* call it on that device again (the looked-up address is kept).             */
 /* ------------------------------------------------------------------------ */
 #define MP_NOALLOC_MAX_POINTS (1 << 17)
 mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef,
@@ -331,7 +333,8 @@ mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off
 /*            coef_off[b] - b + j, plane stride proots                       */
 /*   z0     : NULL or starting values in the same layout (plane stride pz0)  */
 /*   iters, status : DEVICE int32[npoly]                                     */
-/*   ws     : DEVICE workspace of mp_roots_workspace_P(npoly) bytes          */
+/*   ws     : DEVICE workspace of mp_roots_workspace_P(npoly) bytes, 8-byte  */
+/*            aligned (its first word is the 64-bit work-queue counter)      */
 /*   opts->max_degree : host upper bound of the degrees (> 0 required; the   */
 /*            kernel skips, with status 4, any polynomial above it); at most */
 /*            mp_roots_max_degree_P()                                        */

@@ -31,6 +31,8 @@
 // each other and to the next pass.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "mp_arith.cuh"
 #include "mp_common.cuh"
 
@@ -435,16 +437,17 @@ static mp_status polyeval_backward_launch(int64_t npoly, const int64_t *coef_off
     if (npoly == 0) return MP_OK;
     if (coef_off == nullptr || coef == nullptr || pc < 1) return MP_EINVAL;
     if (total > 0 && (!planes_ok(x, total, px) || !planes_ok(dy, total, pdy))) return MP_EINVAL;
+    // every argument check before the first launch: an error return enqueues nothing
+    if (dx && total > 0 && pdx < total) return MP_EINVAL;
+    if (dcoef && pdc < 1) return MP_EINVAL;
+    if (dcoef && total > 0 && (ws == nullptr || ws_bytes < backward_ws<P>(npoly, npts))) return MP_ENOMEM;
     if (dx && total > 0) {
-        if (pdx < total) return MP_EINVAL;
         k_poly_dx<P><<<grid_for(total, 256, 8), 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, x,
                                                                          px, dy, pdy, dx, pdx);
         mp_status st = launch_status();
         if (st != MP_OK) return st;
     }
     if (dcoef) {
-        if (pdc < 1) return MP_EINVAL;
-        if (total > 0 && (ws == nullptr || ws_bytes < backward_ws<P>(npoly, npts))) return MP_ENOMEM;
         const int64_t blocks = (npoly + DCOEF_WARPS - 1) / DCOEF_WARPS;
         k_poly_dcoef<P><<<(unsigned)blocks, 32 * DCOEF_WARPS, 0, as_stream(s)>>>(
             npoly, coef_off, npts, x, px, dy, pdy, dcoef, pdc, static_cast<typename P::T *>(ws), total);
@@ -633,15 +636,21 @@ static __device__ __align__(256) double mp_noalloc_scratch[(size_t)MP_NOALLOC_MA
 
 namespace {
 
-// Device address of mp_noalloc_scratch, looked up once per device (host code
-// cannot use the array's name as a device pointer).
+// Device address of mp_noalloc_scratch, looked up once per device with that
+// device current (host code cannot use the array's name as a device pointer).
+// Host threads may call concurrently: the lookup and the cache are guarded by a
+// mutex.  The cache is not refreshed after cudaDeviceReset (which unloads the
+// library's device code and may move the array): a process that resets a device
+// must not call this entry point on that device again.
 mp_status noalloc_scratch(double **out)
 {
+    static std::mutex mu;
     static double *addr[64] = {nullptr};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
     if (dev < 0 || dev >= 64) return MP_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
     if (addr[dev] == nullptr) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, mp_noalloc_scratch);

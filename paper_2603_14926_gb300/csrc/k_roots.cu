@@ -191,7 +191,7 @@ template <class P> struct DKArgs {
     long long watchdog;
     int32_t max_degree;
     const int32_t *order;  // nullptr: natural order
-    int *counter;          // persistent work queue
+    unsigned long long *counter;  // persistent work queue (64-bit: pops past the end never wrap)
 };
 
 // block-wide max of two doubles and OR of a flag; result in sh
@@ -584,14 +584,14 @@ __global__ void __launch_bounds__(256, DKLaunch<E>::min_blocks) k_dk_persistent(
 {
     extern __shared__ __align__(16) double dk_smem[];
     __shared__ DKShared sh;
-    __shared__ int next;
+    __shared__ unsigned long long next;
     for (;;) {
-        if (threadIdx.x == 0) next = atomicAdd(A.counter, 1);
+        if (threadIdx.x == 0) next = atomicAdd(A.counter, 1ull);
         __syncthreads();
-        const int64_t p = next;
+        const unsigned long long p = next;
         __syncthreads();
-        if (p >= A.npoly) break;
-        dk_solve<P, E>(A, A.order ? A.order[p] : p, sh, dk_smem);
+        if (p >= (unsigned long long)A.npoly) break;
+        dk_solve<P, E>(A, A.order ? A.order[p] : (int64_t)p, sh, dk_smem);
     }
 }
 
@@ -686,7 +686,7 @@ static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npol
         }
         int64_t grid = (int64_t)sm_count() * per_sm;
         if (grid > npoly) grid = npoly;
-        e = cudaMemsetAsync(A.counter, 0, sizeof(int), st);
+        e = cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return cuda_status(e);
         k_dk_persistent<P, E><<<(unsigned)grid, threads, smem, st>>>(A);
         return launch_status();
@@ -720,7 +720,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
                                                  : DKLaunch<NativeEngine<double>>::default_threads);
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
-    if (ws == nullptr) return MP_EINVAL;
+    if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 8 != 0) return MP_EINVAL;
     if (ws_bytes < dk_ws(npoly)) return MP_ENOMEM;
     cudaStream_t st = as_stream(s);
     DKArgs<P> A{};
@@ -741,7 +741,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
     A.radius = o->radius;
     A.watchdog = o->watchdog_cycles;
     A.max_degree = o->max_degree;
-    A.counter = static_cast<int *>(ws);
+    A.counter = static_cast<unsigned long long *>(ws);
     int32_t *order = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + 256);
     A.order = nullptr;
     const size_t smem = dk_smem_bytes<P>(o->max_degree);

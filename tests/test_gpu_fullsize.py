@@ -116,3 +116,52 @@ def test_roots_at_max_degree(mp, oracle):
     wr, wit, wst = oracle.roots("qd", prob.coef_off, coef, radius=1.1, max_iter=1)
     assert host(it)[0] == wit[0] == 1 and host(st)[0] == wst[0]
     assert same_bits(host(r), wr)
+
+
+def _sample_pairs(n, count, seed):
+    """Corners, edge midpoints and random entries of an n x n result."""
+    rng = np.random.default_rng(seed)
+    fixed = [(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (n // 2, 0), (0, n // 2), (n // 2, n - 1),
+             (n - 1, n // 2)]
+    rand = list(zip(rng.integers(0, n, count - len(fixed)).tolist(), rng.integers(0, n, count - len(fixed)).tolist()))
+    return fixed + rand
+
+
+def test_gemm_backward_qd_2048_sampled(mp, oracle):
+    """The GEMM adjoint at the benchmark's size (QD, n = 2048) through the
+    torch.autograd.Function: 40 sampled entries each of dA = dC B^T and
+    dB = A^T dC (the transposed-operand TMA path) bit for bit against the
+    oracle's GEMM with op = T on the entry's row and column."""
+    import torch
+
+    from paper_2603_14926_gb300.autograd import mp_gemm
+
+    prec, K, n = "qd", 4, 2048
+    A = inputs.mp_uniform(11, (n, n), K)
+    B = inputs.mp_uniform(12, (n, n), K)
+    G = inputs.mp_uniform(13, (n, n), K)
+    tA = dev(A).requires_grad_(True)
+    tB = dev(B).requires_grad_(True)
+    C = mp_gemm(prec, tA, tB)
+    dA, dB = torch.autograd.grad(C, (tA, tB), dev(G))
+    dA, dB = host(dA), host(dB)
+    for i, j in _sample_pairs(n, 40, 1):
+        want = oracle.gemm(prec, G[:, i:i + 1, :], B[:, j:j + 1, :], opB=1)[:, 0, 0]
+        assert same_bits(dA[:, i, j], want), ("dA", i, j)
+    for i, j in _sample_pairs(n, 40, 2):
+        want = oracle.gemm(prec, A[:, :, i:i + 1], G[:, :, j:j + 1], opA=1)[:, 0, 0]
+        assert same_bits(dB[:, i, j], want), ("dB", i, j)
+
+
+@pytest.mark.parametrize("prec,n", [("tf", 4096), ("qf", 4096), ("td", 2048)])
+def test_gemm_benchmark_sizes_sampled(mp, oracle, prec, n):
+    """The square GEMM sizes the benchmark reports beyond QD 2048 / DD 4096: the
+    binary32-component variants at n = 4096 and TD at n = 2048, built-in
+    configuration, 32 sampled entries bit for bit."""
+    K, dt = oracle.PRECS[prec]
+    A = inputs.mp_uniform(2, (n, n), K, dt, stream=inputs.STREAM_A)
+    B = inputs.mp_uniform(2, (n, n), K, dt, stream=inputs.STREAM_B)
+    C = host(mp.gemm(prec, dev(A), dev(B), config=-1))
+    for i, j in _sample_pairs(n, 32, 3):
+        want = oracle.gemm(prec, A[:, i:i + 1, :], B[:, :, j:j + 1])[:, 0, 0]
+        assert same_bits(C[:, i, j], want), (i, j)

@@ -7,8 +7,9 @@ only inputs and outputs.
 The test calls it through the C ABI twice in a row, on two different problems,
 and checks each result bit for bit against mp_polyeval_backward_qd (the entry
 point that takes a caller workspace) -- the tolerance the Horner adjoint's
-parity tests use.  It also checks the size limit.  This file is collected last
-so that a run stopping at the first failure has already run every other test.
+parity tests use -- and the first result also against the CPU oracle's
+adjoint.  It also checks the size limit.  This file is collected last so that a
+run stopping at the first failure has already run every other test.
 """
 
 import ctypes
@@ -71,7 +72,7 @@ def _same(a, b):
                                                  np.ascontiguousarray(b).view(np.uint64))
 
 
-def test_noalloc_matches_workspace_entry_point_twice(mp):
+def test_noalloc_matches_workspace_entry_point_twice(mp, oracle):
     # call 1: 9 polynomials of degree 0..70 at 300 points (three 32-coefficient sweeps)
     # call 2: a different problem that fills the whole scratch (32 x 4096 points)
     for seed, npoly, dmin, dmax, npts in ((11, 9, 0, 70, 300), (12, 32, 20, 40, MAX_POINTS // 32)):
@@ -80,6 +81,9 @@ def test_noalloc_matches_workspace_entry_point_twice(mp):
         want_c, want_x = _with_workspace(mp, off, coef, npts, x, dy)
         assert _same(got_c, want_c), seed
         assert _same(got_x, want_x), seed
+        if seed == 11:  # and the first call against the CPU oracle's adjoint directly
+            ref_c, ref_x = oracle.polyeval_backward("qd", off, coef, npts, x, dy)
+            assert _same(got_c, ref_c) and _same(got_x, ref_x)
 
 
 def test_noalloc_rejects_oversize_requests(mp):
