@@ -68,7 +68,8 @@ def test_cpu_baseline_rows_beside_gpu_rows():
               "estrin_fwd": {"ms": 566.0}, "horner_bwd": {"ms": 956.0},
               "complex_gemm_3m": {"complex_qd_ops_per_s": 1.28e10},
               "gemm_strassen": {"n4096_cutoff2048": {"classical_equiv_qd_ops_per_s": 1.25e10}},
-              "durand_kerner": {"root_sweeps_per_s": 1.3e6}, "chebyshev_dk": {"single_solve_gpu_s": 0.33}}
+              "durand_kerner": {"root_sweeps_per_s": 1.3e6},
+              "chebyshev_dk": {"single_solve_gpu_s": 0.33, "precision": "qd", "sweeps": 230}}
         rows = bench.cpu_baseline_rows(pool, ex)
     finally:
         pool.close()
@@ -76,4 +77,6 @@ def test_cpu_baseline_rows_beside_gpu_rows():
     for key, r in rows.items():
         assert r["sample"] and r["gpu_over_oracle"] > 0, key
     assert rows["axpy"]["gpu_elements_per_s"] == (1 << 24) / 3.2e-3
+    # the Chebyshev ratio compares equal work: the oracle's solve took the GPU's 230 sweeps
+    assert rows["chebyshev_dk"]["sweeps"] == 230 and rows["chebyshev_dk"]["same_work"]
     assert rows["chebyshev_dk"]["gpu_over_oracle"] == rows["chebyshev_dk"]["single_solve_s"] / 0.33
