@@ -395,16 +395,49 @@ def gemm_profile_name(prec, n, hybrid):
     return f"k_gemm_{'hybrid_' if hybrid else ''}{prec}_{n}.md"
 
 
-def gemm_traffic(prec, n, hybrid):
-    """DRAM bytes per launch recorded by ncu for this kernel and size, if any."""
-    path = os.path.join(ROOT, "profiles", gemm_profile_name(prec, n, hybrid))
+def profile_value(name, key, cast=float):
+    """A `key: value` line of the ncu summary profiles/<name>, or None."""
     try:
-        for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                return int(line.split(":", 1)[1].strip())
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if line.startswith(key + ":"):
+                return cast(line.split(":", 1)[1].strip())
     except OSError:
         pass
     return None
+
+
+def gemm_traffic(prec, n, hybrid):
+    """DRAM bytes per launch recorded by ncu for this kernel and size, if any."""
+    return profile_value(gemm_profile_name(prec, n, hybrid), "traffic_bytes_per_launch", int)
+
+
+def gemm_pipes(prec, n, hybrid, launch_s, fp64_achieved_g, fp64_nominal_g, fp64_live_g):
+    """Both pipes the hybrid GEMM loads: FP64 instructions/s against the FP64
+    pipe, and integer instructions/s against the integer ALU pipe and the FMA
+    pipe's integer rate (each measured live with the pipe microbenchmark), using
+    the per-multiply-add lane-instruction counts of this kernel's ncu summary
+    (sm__inst_executed_pipe_alu / _fma x 32 / n^3; they do not depend on n)."""
+    name = gemm_profile_name(prec, n, hybrid)
+    alu = profile_value(name, "alu_lane_instr_per_mac")
+    fma = profile_value(name, "fma_lane_instr_per_mac")
+    out = {"fp64": {"instr_per_mac": mac_instr_hybrid(prec) if hybrid else mac_instr(prec),
+                    "achieved_G_per_s": fp64_achieved_g, "peak_nominal_G_per_s": fp64_nominal_g,
+                    "peak_measured_live_G_per_s": fp64_live_g,
+                    "frac_of_nominal": fp64_achieved_g / fp64_nominal_g,
+                    "frac_of_measured": fp64_achieved_g / fp64_live_g}}
+    if alu is None or fma is None:
+        out["integer"] = None
+        return out
+    live = int_pipe_peaks_live()
+    for key, per_mac in (("alu", alu), ("fma", fma)):
+        rate = n ** 3 * per_mac / launch_s
+        out[key] = {"lane_instr_per_mac": per_mac, "achieved_T_per_s": rate / 1e12,
+                    "peak_measured_live_T_per_s": live[key] / 1e12, "frac_of_measured": rate / live[key]}
+    out["source"] = (f"per-multiply-add counts: profiles/{name}; peaks: mp_peak_run kinds 0 (DFMA), "
+                     "7 (LOP3, integer ALU pipe) and 8 (IMAD, FMA pipe) run in this process")
+    out["bound"] = max(("fp64", out["fp64"]["frac_of_measured"]), ("alu", out["alu"]["frac_of_measured"]),
+                       ("fma", out["fma"]["frac_of_measured"]), key=lambda kv: kv[1])[0]
+    return out
 
 
 def measured_hbm_gbs():
@@ -421,6 +454,24 @@ def fp64_peak_live():
     mpg.peak(0, iters=256)
     rate, _ = mpg.peak(0, iters=4096)
     return rate
+
+
+def int_pipe_peaks_live():
+    """Lane instructions/s of the integer ALU pipe (LOP3 chains) and of integer
+    work on the FMA pipe (IMAD chains), measured now with the pipe
+    microbenchmark (mp_peak_run kinds 7 and 8), best of two launch shapes."""
+    import paper_2603_14926_gb300 as mpg
+
+    sms = mpg.lib().mp_sm_count()
+    out = {}
+    for kind, name in ((7, "alu"), (8, "fma")):
+        best = 0.0
+        for per_sm, thr in ((4, 256), (8, 256)):
+            mpg.peak(kind, iters=1024, blocks=sms * per_sm, threads=thr)
+            rate, _ = mpg.peak(kind, iters=65536, blocks=sms * per_sm, threads=thr)
+            best = max(best, rate)
+        out[name] = best
+    return out
 
 
 def extras(prec="qd", quick=False):
@@ -1010,6 +1061,11 @@ def run_gpu(a, rank, world, pool):
                 "fp64_instr_per_mac": mac_instr_hybrid(prec) if hybrid else mac_instr(prec),
                 "paper_fp64_instr_per_mac": mac_instr(prec),
                 "paper_sequence_equiv_instr_per_s": n ** 3 * mac_instr(prec) / launch_s / 1e9,
+                "paper_sequence_equiv_note": "n^3 x the paper's all-FP64 instruction count per multiply-add "
+                                             "/ launch time: the rate at which that sequence's results are "
+                                             "reproduced; part of it runs on the integer pipes, so this is "
+                                             "not a fraction of any one pipe",
+                "pipes": gemm_pipes(prec, n, hybrid, launch_s, achieved, peak_nominal, peak_live),
                 "algorithmic_instr_per_launch": instr, "launch_ms": launch_s * 1e3,
                 "traffic": gemm_traffic(prec, n, hybrid),
                 "traffic_source": f"profiles/{gemm_profile_name(prec, n, hybrid)} (ncu dram__bytes_read.sum + "
