@@ -370,6 +370,11 @@ typedef struct {
                            const mp_roots_opts *opts, void *ws, size_t ws_bytes,             \
                            mp_stream stream);
 
+/* mp_roots_hybrid_fallbacks: how many root updates, over all precisions and  */
+/* calls since the library was loaded, left the hybrid engine's domain and    */
+/* were recomputed on the FP64 pipe (same bits either way).  SYNCHRONIZES.   */
+mp_status mp_roots_hybrid_fallbacks(unsigned long long *count);
+
 /* mp_roots_init_P writes the Eq. 5 starting values (or radius-r circle) that */
 /* mp_roots_P uses when z0 == NULL, as a complex K-array (lower components 0). */
 

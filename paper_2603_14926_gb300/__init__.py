@@ -121,6 +121,8 @@ def _declare(L):
         f.argtypes = [_i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp,
                       ctypes.POINTER(RootsOpts), _vp, ctypes.c_size_t, _vp]
         f.restype = _int
+    L.mp_roots_hybrid_fallbacks.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+    L.mp_roots_hybrid_fallbacks.restype = _int
     L.mp_peak_run.argtypes = [_int, _i64, _int, _int, ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_double), _vp]
     L.mp_peak_run.restype = _int
@@ -473,6 +475,14 @@ def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_w
           z0.stride(0) if z0 is not None else 0, _ptr(r), r.stride(0), _ptr(iters),
           _ptr(status), ctypes.byref(o), _ptr(ws), ws.numel(), _stream())
     return r[:, :total], iters, status
+
+
+def roots_hybrid_fallbacks():
+    """Root updates recomputed on the FP64 pipe since the library was loaded
+    (the hybrid engine left its domain; synchronizes)."""
+    v = ctypes.c_ulonglong()
+    _call("mp_roots_hybrid_fallbacks", ctypes.byref(v))
+    return v.value
 
 
 class RootsGraph:

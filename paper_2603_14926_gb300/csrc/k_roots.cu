@@ -225,6 +225,17 @@ __device__ void block_max2(DKShared &sh, double a, double b, int bad)
     __syncthreads();
 }
 
+// The hybrid engine of the solver packs subnormal TwoSum error terms too: the
+// imaginary parts of iterates converging to real roots fall through the bottom
+// of the binary64 range within a few sweeps, and with the default engine every
+// such root was recomputed on the FP64 pipe (about 46,000 roots per sweep of the
+// batched workload, each a full update run by a few lanes of a warp).
+using DKHybrid = HybridEngine<false, false, true>;
+
+// Roots recomputed on the FP64 pipe because the hybrid engine left its domain
+// (all precisions; read by mp_roots_hybrid_fallbacks).
+static __device__ unsigned long long mp_dk_fallbacks;
+
 // The hybrid engine's multicomponent add and multiply, called out of line.  The
 // root update holds about fifteen of them per step; inlined, the hybrid code
 // overflows the instruction cache.  Each call runs its own engine and hands its
@@ -237,7 +248,7 @@ template <class P> struct HybridResult {
 template <class P>
 __device__ __noinline__ HybridResult<P> hybrid_add_call(typename P::V a, typename P::V b)
 {
-    HybridEngine<false> h;
+    DKHybrid h;
     const typename P::V r = P::add(a, b, h);
     return {r, h.bad};
 }
@@ -245,7 +256,7 @@ __device__ __noinline__ HybridResult<P> hybrid_add_call(typename P::V a, typenam
 template <class P>
 __device__ __noinline__ HybridResult<P> hybrid_mul_call(typename P::V a, typename P::V b)
 {
-    HybridEngine<false> h;
+    DKHybrid h;
     const typename P::V r = P::mul(a, b, h);
     return {r, h.bad};
 }
@@ -254,13 +265,13 @@ __device__ __noinline__ HybridResult<P> hybrid_mul_call(typename P::V a, typenam
 // (the native engine stays inline).
 template <class P> struct OutlinedHybrid : P {
     using V = typename P::V;
-    static __device__ __forceinline__ V add(const V &a, const V &b, HybridEngine<false> &g)
+    static __device__ __forceinline__ V add(const V &a, const V &b, DKHybrid &g)
     {
         const HybridResult<P> r = hybrid_add_call<P>(a, b);
         g.bad |= r.bad;
         return r.v;
     }
-    static __device__ __forceinline__ V mul(const V &a, const V &b, HybridEngine<false> &g)
+    static __device__ __forceinline__ V mul(const V &a, const V &b, DKHybrid &g)
     {
         const HybridResult<P> r = hybrid_mul_call<P>(a, b);
         g.bad |= r.bad;
@@ -479,7 +490,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
         int bad = 0;
         const int rot = nwarps > 1 ? 32 * (int)((b + k) % nwarps) : 0;
         const int vt = (tid + nt - rot) % nt;  // this thread's place in the dealing order
-        using PU = typename std::conditional<std::is_same<E, HybridEngine<false>>::value, OutlinedHybrid<P>, P>::type;
+        using PU = typename std::conditional<std::is_same<E, DKHybrid>::value, OutlinedHybrid<P>, P>::type;
         if (split) {
             // Two threads per root: places poff .. poff+n-1 of the dealing order run
             // the product chains and leave them in the root's next-iterate slot,
@@ -513,7 +524,10 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
                 const V dr = vload<P>(zn, pn, i), di = vload<P>(zn + K * pn, pn, i);
                 V yr, yi, wr, wi;
                 dk_finish<PU>(hr, hi, Eq, dr, di, sh.split_e[i], zr, zi, yr, yi, wr, wi, g);
-                if (g.failed() || sh.split_bad[i]) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                if (g.failed() || sh.split_bad[i]) {
+                    atomicAdd(&mp_dk_fallbacks, 1ull);
+                    dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                }
                 vstore<P>(zn, pn, i, yr);
                 vstore<P>(zn + K * pn, pn, i, yi);
                 const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
@@ -528,7 +542,10 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
                 V yr, yi, wr, wi;
                 E g;
                 dk_update<PU>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, g);
-                if (g.failed()) dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                if (g.failed()) {
+                    atomicAdd(&mp_dk_fallbacks, 1ull);
+                    dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+                }
                 vstore<P>(zn, pn, i, yr);
                 vstore<P>(zn + K * pn, pn, i, yi);
                 const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
@@ -575,7 +592,7 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
 template <class E> struct DKLaunch {
     static constexpr int min_blocks = 0, default_threads = 128;
 };
-template <bool Q> struct DKLaunch<HybridEngine<Q>> {
+template <> struct DKLaunch<DKHybrid> {
     static constexpr int min_blocks = 2, default_threads = 256;
 };
 
@@ -716,7 +733,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
     if (o->engine < 0 || o->engine > 2) return MP_EINVAL;
     const bool hybrid = o->engine != 2;  // 0 = automatic: the hybrid engine
     const int threads = o->threads > 0 ? o->threads
-                                       : (hybrid ? DKLaunch<HybridEngine<false>>::default_threads
+                                       : (hybrid ? DKLaunch<DKHybrid>::default_threads
                                                  : DKLaunch<NativeEngine<double>>::default_threads);
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
@@ -751,7 +768,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         if (e != MP_OK) return e;
         A.order = order;
     }
-    return hybrid ? dk_run<P, HybridEngine<false>>(A, o, npoly, threads, smem, st)
+    return hybrid ? dk_run<P, DKHybrid>(A, o, npoly, threads, smem, st)
                   : dk_run<P, NativeEngine<double>>(A, o, npoly, threads, smem, st);
 }
 
@@ -794,6 +811,12 @@ extern "C" {
         return roots_launch<PT>(npoly, coef_off, coef, pcoef, z0, pz0, roots, proots, iters, status,  \
                                 opts, ws, ws_bytes, s);                                               \
     }
+
+mp_status mp_roots_hybrid_fallbacks(unsigned long long *count)
+{
+    if (count == nullptr) return MP_EINVAL;
+    return cuda_status(cudaMemcpyFromSymbol(count, mp_dk_fallbacks, sizeof(unsigned long long)));
+}
 
 MP_EXPORT_ROOTS(dd, P_dd)
 MP_EXPORT_ROOTS(ddc, P_ddc)

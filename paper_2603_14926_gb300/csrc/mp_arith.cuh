@@ -86,7 +86,8 @@ __device__ __forceinline__ void two_prod(T a, T b, T &p, T &e)
 //   from the integer pipes (mp_eft_int.cuh); with QTS also QuickTwoSum's error
 //   where Algorithm 1 is exact (exponent(a) >= exponent(b), or a zero operand);
 //   with TP also TwoProd's error (p from one FP64 multiply, the error term from
-//   the low 64 bits of the integer significand product).  The plain operations
+//   the low 64 bits of the integer significand product); with SUB also a
+//   subnormal TwoSum error term.  The plain operations
 //   stay on the FP64 pipe.  Outside the
 //   integer path's domain, and for QuickTwoSum outside its exact case, the
 //   engine raises failed(); callers then recompute the result with
@@ -102,14 +103,14 @@ template <typename T> struct NativeEngine {
     __device__ __forceinline__ bool failed() const { return false; }
 };
 
-template <bool QTS, bool TP = false> struct HybridEngine {
+template <bool QTS, bool TP = false, bool SUB = false> struct HybridEngine {
     uint32_t bad = 0;
     __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e)
     {
         const double s_ = __dadd_rn(a, b);
-        e = __longlong_as_double((long long)eft_int::two_sum_err((uint64_t)__double_as_longlong(a),
-                                                                  (uint64_t)__double_as_longlong(b),
-                                                                  (uint64_t)__double_as_longlong(s_), bad));
+        e = __longlong_as_double((long long)eft_int::two_sum_err<SUB>((uint64_t)__double_as_longlong(a),
+                                                                       (uint64_t)__double_as_longlong(b),
+                                                                       (uint64_t)__double_as_longlong(s_), bad));
         s = s_;
     }
     __device__ __forceinline__ void quick_two_sum(double a, double b, double &s, double &e)

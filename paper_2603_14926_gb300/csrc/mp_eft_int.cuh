@@ -22,7 +22,8 @@
 //   - e is zero or normal.
 // Outside that domain the function raises `bad`; callers then recompute the whole
 // result with the FP64 pipe, so every output stays exactly the paper's operation
-// sequence.
+// sequence.  A variant (SUBNORMAL) also packs a subnormal e exactly, for callers
+// whose values reach the bottom of the binary64 range.
 //
 // The functions are also compiled for the host, where a unit test checks them
 // against the host's binary64 arithmetic.
@@ -110,7 +111,11 @@ MP_HD void unpack(uint64_t x, int &e1, uint64_t &m)
 }
 
 // e = a + b - s for s = fl(a + b), as a binary64 pattern.  `bad` is raised when
-// the operands leave the domain stated above.
+// the operands leave the domain stated above.  With SUBNORMAL the domain also
+// takes in a subnormal e (the error of a sum of tiny operands): e is a multiple
+// of 2^(u - 1075) below 2^-1022, so its fraction field is exactly mag * 2^(u - 1);
+// the domain is then only "a and b finite with biased exponent <= 2045".
+template <bool SUBNORMAL = false>
 MP_HD uint64_t two_sum_err(uint64_t A, uint64_t B, uint64_t S, uint32_t &bad)
 {
     int ea, eb, es;
@@ -147,6 +152,11 @@ MP_HD uint64_t two_sum_err(uint64_t A, uint64_t B, uint64_t S, uint32_t &bad)
     const uint32_t eh = (f + (uint32_t)(be - 1) * hb) | (hi32(kn) & 0x80000000u);
     const uint32_t el = shr11_lo(nl, nh);
     // |s| <= 2 max(|a|, |b|), so exponents of a and b <= 2045 bound s's by 2046
+    if (SUBNORMAL) {
+        bad |= (uint32_t)(imax(ea, eb) > 2045);
+        const uint64_t sub = shl_mod(mag, (uint32_t)(u - 1)) | (kn & 0x8000000000000000ull);
+        return (hb != 0 && be < 1) ? sub : mk64(eh, el);
+    }
     bad |= (uint32_t)(imax(ea, eb) > 2045) | (uint32_t)(hb != 0 && be < 1);
     return mk64(eh, el);
 }

@@ -1,7 +1,8 @@
 // Host check of the integer-pipe TwoSum error term (mp_eft_int.cuh) against the
 // host's binary64 arithmetic: for every pair the function accepts (bad == 0) its
 // result must equal e = (a - (s - v)) + (b - v), v = s - a, s = a + b bit for
-// bit (Algorithm 2); inside the documented domain it must accept.
+// bit (Algorithm 2); inside the documented domain it must accept.  Both forms:
+// the default one and the one that also packs subnormal error terms.
 //   usage: eft_int_check <pairs> <seed>     exit 0 = pass
 #define __host__
 #define __device__
@@ -40,6 +41,7 @@ static double random_frac_double(int emin, int emax)
 }
 
 static long checked = 0, accepted = 0, wrong = 0, refused_in_domain = 0;
+static long schecked = 0, saccepted = 0, swrong = 0, srefused = 0;
 static long pchecked = 0, paccepted = 0, pwrong = 0, prefused = 0;
 
 // TwoProd error term against the host's correctly rounded fma
@@ -88,6 +90,33 @@ static void check(double a, double b, bool in_domain)
     }
 }
 
+// The variant that also packs subnormal error terms: its domain is only "both
+// exponents <= 2045" (tiny and subnormal operands included).
+static void check_sub(double a, double b)
+{
+    volatile double s = a + b;
+    volatile double v = s - a;
+    volatile double t = s - v;
+    volatile double x = a - t, y = b - v;
+    const double e = x + y;
+    uint32_t bad = 0;
+    const uint64_t got = mp::eft_int::two_sum_err<true>(bits(a), bits(b), bits(s), bad);
+    const bool in_domain = ((bits(a) >> 52) & 0x7FF) <= 2045 && ((bits(b) >> 52) & 0x7FF) <= 2045;
+    schecked++;
+    if (bad) {
+        if (in_domain) {
+            if (srefused < 5) std::printf("subnormal variant refused in domain: a=%a b=%a\n", a, b);
+            srefused++;
+        }
+        return;
+    }
+    saccepted++;
+    if (got != bits(e)) {
+        if (swrong < 10) std::printf("subnormal variant wrong: a=%a b=%a  got %a  want %a\n", a, b, dbl(got), e);
+        swrong++;
+    }
+}
+
 int main(int argc, char **argv)
 {
     const long pairs = argc > 1 ? std::atol(argv[1]) : 1000000;
@@ -98,6 +127,7 @@ int main(int argc, char **argv)
     for (double a : special)
         for (double b : special) {
             check(a, b, false);
+            check_sub(a, b);
             check_prod(a, b, false);
         }
     for (long i = 0; i < pairs; i++) {
@@ -133,6 +163,13 @@ int main(int argc, char **argv)
             if (e != 0 && std::fabs(e) < 0x1p-1022) dom = false;
         }
         check(a, b, dom);
+        check_sub(a, b);
+        if (mode == 7) {  // the subnormal range proper: both operands below 2^-1000, gaps 0..60
+            const double c = random_frac_double(0, 22);
+            const double d = random_frac_double(0, 22);
+            check_sub(c, d);
+            check_sub(c, -d);
+        }
         // products: exponents spread around the range, ties and zeros included
         {
             double c = random_frac_double(1, 2046), d;
@@ -157,5 +194,7 @@ int main(int argc, char **argv)
     std::printf("checked %ld accepted %ld wrong %ld refused-in-domain %ld\n", checked, accepted, wrong, refused_in_domain);
     std::printf("products: checked %ld accepted %ld wrong %ld refused-in-domain %ld\n", pchecked, paccepted, pwrong,
                 prefused);
-    return (wrong || refused_in_domain || pwrong || prefused) ? 1 : 0;
+    std::printf("subnormal variant: checked %ld accepted %ld wrong %ld refused-in-domain %ld\n", schecked, saccepted,
+                swrong, srefused);
+    return (wrong || refused_in_domain || pwrong || prefused || swrong || srefused) ? 1 : 0;
 }

@@ -1,7 +1,10 @@
 """The integer-pipe TwoSum error term (csrc/mp_eft_int.cuh), compiled for the host
 with g++, against the host's binary64 arithmetic (Algorithm 2): every accepted
 pair must give Algorithm 2's error term bit for bit, and every pair inside the
-documented domain must be accepted.  Independent of the oracle and of the GPU."""
+documented domain must be accepted -- for the default form, for the variant
+that also packs subnormal error terms (whose domain takes in tiny and subnormal
+operands), and for the TwoProd error term.  Independent of the oracle and of the
+GPU."""
 
 import os
 import shutil
@@ -28,4 +31,5 @@ def checker(tmp_path_factory):
 def test_two_sum_error_term_matches_binary64(checker, seed):
     r = subprocess.run([checker, "2000000", str(seed)], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "wrong 0 refused-in-domain 0" in r.stdout
+    lines = [ln for ln in r.stdout.splitlines() if "checked" in ln]
+    assert len(lines) == 3 and all("wrong 0 refused-in-domain 0" in ln for ln in lines), r.stdout

@@ -161,10 +161,11 @@ def test_roots_bit_exact(mp, oracle, prec, engine):
 @pytest.mark.parametrize("prec", ["dd", "td", "qd"])
 def test_roots_range_limits_bit_exact(mp, oracle, prec):
     """Hybrid engine (the default).  One starting value per polynomial placed
-    near 2^-1000 makes the first sweep's Horner products leave the hybrid engine's
-    domain (subnormal error terms): that root is recomputed on the FP64 pipe, and roots, sweep counts and
-    statuses stay bit-identical to the oracle.  (Two such starting values would
-    make a difference underflow to zero and the solve break down.)"""
+    near 2^-1000 makes the first sweep's Horner products produce subnormal TwoSum
+    error terms, which the solver's hybrid engine packs exactly on the integer
+    pipes (no FP64 recomputation): roots, sweep counts and statuses stay
+    bit-identical to the oracle.  (Two such starting values would make a
+    difference underflow to zero and the solve break down.)"""
     K = oracle.PRECS[prec][0]
     prob = inputs.dk_problem(5, 4, 12, 30)
     coef = oracle.poly_from_roots(prec, prob)
@@ -174,12 +175,34 @@ def test_roots_range_limits_bit_exact(mp, oracle, prec):
         z = oracle.aberth(prec, c, radius=1.1)
         z[:, :1] *= 2.0 ** -1000
         z0[:, prob.root_off[b]:prob.root_off[b + 1]] = z
+    before = mp.roots_hybrid_fallbacks()
     r, it, st = mp.roots(prec, dev(prob.coef_off), dev(coef), int(prob.degrees.max()), z0=dev(z0), max_iter=40,
                          engine=1)
     wr, wit, wst = oracle.roots(prec, prob.coef_off, coef, z0=z0, max_iter=40)
     assert np.array_equal(host(it), wit) and np.array_equal(host(st), wst)
     assert np.isfinite(wr).all() and np.all(wst != 4)
     assert same_bits(np.ascontiguousarray(host(r)), wr)
+    assert mp.roots_hybrid_fallbacks() == before
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_roots_fp64_recomputation_bit_exact(mp, oracle, prec):
+    """Starting values near 2^1023 for linear polynomials put TwoSum operands
+    above the hybrid engine's exponent bound (Horner's z + a_0 and the update
+    z - w): those roots are recomputed on the FP64 pipe (counted), and the
+    results, sweep counts and statuses equal the oracle's."""
+    K = oracle.PRECS[prec][0]
+    prob = inputs.dk_problem_from_roots([([], 0.25), ([], -0.75), ([], 0.125)])
+    coef = oracle.poly_from_roots(prec, prob)
+    z0 = np.zeros((2 * K, int(prob.degrees.sum())))
+    z0[0, :] = [2.0 ** 1023, -(2.0 ** 1022) * 1.5, 1.75 * 2.0 ** 1023]
+    before = mp.roots_hybrid_fallbacks()
+    r, it, st = mp.roots(prec, dev(prob.coef_off), dev(coef), int(prob.degrees.max()), z0=dev(z0), max_iter=60,
+                         engine=1)
+    wr, wit, wst = oracle.roots(prec, prob.coef_off, coef, z0=z0, max_iter=60)
+    assert np.array_equal(host(it), wit) and np.array_equal(host(st), wst)
+    assert same_bits(np.ascontiguousarray(host(r)), wr)
+    assert mp.roots_hybrid_fallbacks() > before
 
 
 @pytest.mark.parametrize("mode,sort,threads,engine", [(0, 0, 64, 2), (0, 1, 256, 2), (1, 0, 128, 2), (1, 1, 32, 2),
