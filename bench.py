@@ -836,6 +836,148 @@ def dk_extra(prec="qd", npoly=4096, sweeps=6, loop_polys=16):
     return res
 
 
+def backward_errors(prec, coef_off, coef, roots, degrees, root_off, coef_off_host):
+    """Per polynomial, the largest backward error over its roots,
+    |q(z)| / sum_i |c_i| |z|^i: q(z) evaluated by the library's complex Horner
+    (K-component arithmetic; its own rounding is at most about (4n + 16) 2^-p of
+    the denominator), the denominator in binary64 from leading components."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+
+    K = mpg.PRECS[prec][0]
+    npoly = len(degrees)
+    md = int(degrees.max())
+    deg = torch.from_numpy(np.asarray(degrees, dtype=np.int64)).cuda()
+    roff = torch.from_numpy(np.asarray(root_off, dtype=np.int64)).cuda()
+    j = torch.arange(md, device="cuda")
+    valid = j[None, :] < deg[:, None]                                   # (npoly, md)
+    src = (roff[:-1, None] + j[None, :]).clamp(max=roots.shape[1] - 1)  # root index per slot
+    xr = torch.where(valid[None], roots[:K][:, src], torch.zeros((), dtype=roots.dtype, device="cuda"))
+    xi = torch.where(valid[None], roots[K:][:, src], torch.zeros((), dtype=roots.dtype, device="cuda"))
+    yr, yi = mpg.polyeval(prec, coef_off, coef, md, xr.reshape(K, -1).contiguous(), xi.reshape(K, -1).contiguous())
+    q = torch.hypot(yr[0], yi[0]).reshape(npoly, md)
+    az = torch.hypot(xr[0], xi[0])                                      # (npoly, md)
+    # sum_i |c_i| |z|^i by Horner on magnitudes, coefficients padded with zeros
+    coff = torch.from_numpy(np.asarray(coef_off_host, dtype=np.int64)).cuda()
+    den = torch.zeros_like(az)
+    for i in range(md, -1, -1):
+        idx = (coff[:-1] + i).clamp(max=coef.shape[1] - 1)
+        ci = torch.where(deg >= i, coef[0][idx].abs(), torch.zeros((), dtype=coef.dtype, device="cuda"))
+        den = den * az + ci[:, None]
+    be = torch.where(valid, q / den, torch.zeros((), dtype=q.dtype, device="cuda")).max(dim=1).values
+    return be.cpu().numpy()
+
+
+def roots_full_extra(prec="qd", npoly=4096, max_iter=1000, loop_polys=8, loop_max_sweeps=100, engine=0,
+                     eq5_polys=256, eq5_max_degree=200):
+    """The batched-root workload solved to the end (4096 QD polynomials, degrees
+    uniform in [10, 500], roots in the unit disk, 1e-30 perturbation, start radius
+    1.1, at most 1000 sweeps) in one persistent launch: roots/s, statuses, sweeps,
+    and each polynomial's backward error against the rounding bound of the
+    evaluation; the per-polynomial launch loop (one single-block launch per
+    polynomial, each running its whole solve: the same device code, so the same
+    bits) on a degree-stratified sample; and a subset solved from Eq. 5's own
+    radius beside the radius-1.1 start."""
+    import torch
+
+    import paper_2603_14926_gb300 as mpg
+    from paper_2603_14926_gb300 import inputs
+
+    K = mpg.PRECS[prec][0]
+    p_bits = 53 * K
+    prob = inputs.dk_problem(3, npoly, 10, 500)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    maxdeg = int(prob.degrees.max())
+    coef = mpg.poly_from_roots(prec, dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), maxdeg,
+                               int(prob.coef_off[-1]))
+    off = dev(prob.coef_off)
+    fb0 = mpg.roots_hybrid_fallbacks()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    r, it, st = mpg.roots(prec, off, coef, maxdeg, radius=1.1, max_iter=max_iter, sort=1, engine=engine)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / 1e3
+    fallbacks = mpg.roots_hybrid_fallbacks() - fb0
+    be = backward_errors(prec, off, coef, r, prob.degrees, prob.root_off, prob.coef_off)
+    it, st, rh = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
+    bound = (4.0 * prob.degrees + 16.0) * 2.0 ** -p_bits
+    roots_total = int(prob.degrees.sum())
+    peak = NOMINAL_FP64_TFLOPS * 1e12 / 2
+    instr = dk_instr(prec, prob.degrees, it, hybrid=engine != 2)
+    out = {"polys": npoly, "degrees": "uniform [10, 500]", "roots": roots_total, "max_sweeps": max_iter,
+           "start": "Eq. 5 centre and angles, radius 1.1", "batched_s": tb, "roots_per_s": roots_total / tb,
+           "launch": "one persistent launch (queue reset, descending-degree order, persistent kernel)",
+           "fp64_instr_frac": instr / tb / peak, "fp64_recomputed_root_updates": int(fallbacks),
+           "sweeps_mean": float(it.mean()), "sweeps_max": int(it.max()),
+           "status_counts": {"cap": int(np.sum(st == 0)), "converged": int(np.sum(st == 1)),
+                             "stagnated": int(np.sum(st == 2)), "breakdown": int(np.sum(st == 4))},
+           "backward_error": {
+               "definition": "per polynomial, max over its roots of |q(z)| / sum_i |c_i| |z|^i "
+                             "(q evaluated in the same K-component arithmetic)",
+               "median": float(np.median(be)), "max": float(be.max()),
+               "median_log2": float(np.log2(np.median(be))) if np.median(be) > 0 else None,
+               "max_log2": float(np.log2(be.max())) if be.max() > 0 else None,
+               "bound": "(4n + 16) 2^-p, the rounding bound of one K-component Horner evaluation",
+               "polys_within_bound": int(np.sum(be <= bound)),
+               "by_status_median_log2": {nm: float(np.log2(np.median(be[st == c]))) for c, nm in
+                                         ((0, "cap"), (1, "converged"), (2, "stagnated")) if np.any(st == c)
+                                         and np.median(be[st == c]) > 0}}}
+    # the per-polynomial launch loop on a degree-stratified sample of the polynomials
+    # the batched solve finished within loop_max_sweeps sweeps (bounded time)
+    cand = np.where(it <= loop_max_sweeps)[0]
+    cand = cand[np.argsort(prob.degrees[cand], kind="stable")]
+    sel = cand[np.linspace(0, len(cand) - 1, loop_polys).astype(int)]
+    hc = coef.cpu().numpy()
+    so = np.zeros(len(sel) + 1, dtype=np.int64)
+    np.cumsum(prob.degrees[sel] + 1, out=so[1:])
+    sc = np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in sel], 1)
+    md = int(prob.degrees[sel].max())
+    mpg.roots(prec, dev(so), dev(sc), md, radius=1.1, max_iter=1, mode=1, engine=engine)
+    torch.cuda.synchronize()
+    e0.record()
+    rl, itl, stl = mpg.roots(prec, dev(so), dev(sc), md, radius=1.1, max_iter=max_iter, mode=1, engine=engine)
+    e1.record()
+    torch.cuda.synchronize()
+    tl = e0.elapsed_time(e1) / 1e3
+    rl = rl.cpu().numpy()
+    same = all(np.array_equal(rl[:, so[q] - q:so[q + 1] - q - 1].view(np.uint64),
+                              np.ascontiguousarray(rh[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
+               for q, b in enumerate(sel))
+    instr_l = dk_instr(prec, prob.degrees[sel], itl.cpu().numpy(), hybrid=engine != 2)
+    out["per_poly_loop"] = {
+        "form": "one single-block launch per polynomial, each running that polynomial's whole solve "
+                "(mp_roots_P mode 1), back to back on one stream",
+        "sample": f"{len(sel)} polynomials stratified by degree among the {len(cand)} the batched solve "
+                  f"finished within {loop_max_sweeps} sweeps",
+        "degrees": prob.degrees[sel].tolist(), "sweeps": itl.cpu().numpy().tolist(), "loop_s": tl,
+        "identical_bits_to_batched": bool(same), "roots_per_s": float(prob.degrees[sel].sum()) / tl,
+        "batched_over_loop_per_unit_work": (instr / tb) / (instr_l / tl)}
+    # Eq. 5's own radius against radius 1.1 on a stratified subset of low degree
+    small = np.where(prob.degrees <= eq5_max_degree)[0]
+    small = small[np.argsort(prob.degrees[small], kind="stable")]
+    sub = small[np.linspace(0, len(small) - 1, min(eq5_polys, len(small))).astype(int)]
+    so = np.zeros(len(sub) + 1, dtype=np.int64)
+    np.cumsum(prob.degrees[sub] + 1, out=so[1:])
+    sc = dev(np.concatenate([hc[:, prob.coef_off[b]:prob.coef_off[b + 1]] for b in sub], 1))
+    dso = dev(so)
+    md = int(prob.degrees[sub].max())
+    eq5 = {"polys": len(sub), "degrees": f"stratified over the workload's degrees <= {eq5_max_degree}"}
+    for name, rad in (("radius_1.1", 1.1), ("eq5_radius", 0.0)):
+        e0.record()
+        r5, i5, s5 = mpg.roots(prec, dso, sc, md, radius=rad, max_iter=max_iter, sort=1, engine=engine)
+        e1.record()
+        torch.cuda.synchronize()
+        i5, s5 = i5.cpu().numpy(), s5.cpu().numpy()
+        eq5[name] = {"s": e0.elapsed_time(e1) / 1e3, "sweeps_mean": float(i5.mean()), "sweeps_max": int(i5.max()),
+                     "status_counts": {"cap": int(np.sum(s5 == 0)), "converged": int(np.sum(s5 == 1)),
+                                       "stagnated": int(np.sum(s5 == 2)), "breakdown": int(np.sum(s5 == 4))}}
+    out["start_radius_comparison"] = eq5
+    return out
+
+
 def chebyshev_extra(prec="qd", n=64, copies=4096, engine=0):
     """The paper's Durand-Kerner problem (Section 4.2, Eq. 6, n = 64; Table 6): one solve
     on the GPU (latency), a batch of `copies` identical problems in one persistent
@@ -1102,15 +1244,27 @@ def run_gpu(a, rank, world, pool):
     if rank == 0 and pool is not None:
         out["cpu_baseline"] = cpu_baseline(pool, prec, n, a.seed)
     if rank == 0 and not a.no_extras:
+        # each leg on its own: a failing leg is reported and never hides the others
+        ex = {}
+        legs = (("kernels", lambda: extras(prec, quick=a.quick)),
+                ("durand_kerner", lambda: dk_extra(prec, npoly=512 if a.quick else 4096)),
+                ("chebyshev_dk", lambda: chebyshev_extra(prec, copies=512 if a.quick else 4096)),
+                ("roots_full", lambda: roots_full_extra(prec, npoly=512 if a.quick else 4096)))
+        for name, fn in legs:
+            try:
+                r = fn()
+                if name == "kernels":
+                    ex.update(r)
+                else:
+                    ex[name] = r
+            except Exception as e:  # noqa: BLE001
+                ex[name + "_error"] = repr(e)
         try:
-            ex = extras(prec, quick=a.quick)
-            ex["durand_kerner"] = dk_extra(prec, npoly=512 if a.quick else 4096)
-            ex["chebyshev_dk"] = chebyshev_extra(prec, copies=512 if a.quick else 4096)
             if pool is not None and "cpu_baseline" in out:
                 out["cpu_baseline"]["rows_one_core"] = cpu_baseline_rows(pool, ex)
-            out["extra"] = ex
-        except Exception as e:  # extras never hide the headline
-            out["extra"] = {"error": repr(e)}
+        except Exception as e:  # noqa: BLE001
+            out["cpu_baseline"]["rows_one_core_error"] = repr(e)
+        out["extra"] = ex
     return out
 
 
