@@ -904,6 +904,8 @@ def roots_full_extra(prec="qd", npoly=4096, max_iter=1000, loop_polys=8, loop_ma
     be = backward_errors(prec, off, coef, r, prob.degrees, prob.root_off, prob.coef_off)
     it, st, rh = it.cpu().numpy(), st.cpu().numpy(), r.cpu().numpy()
     bound = (4.0 * prob.degrees + 16.0) * 2.0 ** -p_bits
+    fin = np.isfinite(be)
+    lg = lambda v: float(np.log2(v)) if v > 0 else None  # noqa: E731
     roots_total = int(prob.degrees.sum())
     peak = NOMINAL_FP64_TFLOPS * 1e12 / 2
     instr = dk_instr(prec, prob.degrees, it, hybrid=engine != 2)
@@ -917,14 +919,17 @@ def roots_full_extra(prec="qd", npoly=4096, max_iter=1000, loop_polys=8, loop_ma
            "backward_error": {
                "definition": "per polynomial, max over its roots of |q(z)| / sum_i |c_i| |z|^i "
                              "(q evaluated in the same K-component arithmetic)",
-               "median": float(np.median(be)), "max": float(be.max()),
-               "median_log2": float(np.log2(np.median(be))) if np.median(be) > 0 else None,
-               "max_log2": float(np.log2(be.max())) if be.max() > 0 else None,
+               "median_log2": lg(np.median(be[fin])) if fin.any() else None,
+               "max_log2": lg(be[fin].max()) if fin.any() else None,
+               "not_finite": {"polys": int(np.sum(~fin)), "statuses": st[~fin].tolist()[:20]},
                "bound": "(4n + 16) 2^-p, the rounding bound of one K-component Horner evaluation",
                "polys_within_bound": int(np.sum(be <= bound)),
-               "by_status_median_log2": {nm: float(np.log2(np.median(be[st == c]))) for c, nm in
-                                         ((0, "cap"), (1, "converged"), (2, "stagnated")) if np.any(st == c)
-                                         and np.median(be[st == c]) > 0}}}
+               "by_status": {nm: {"polys": int(np.sum(st == c)),
+                                  "median_log2": lg(np.median(be[(st == c) & fin])) if np.any((st == c) & fin)
+                                  else None,
+                                  "max_log2": lg(be[(st == c) & fin].max()) if np.any((st == c) & fin) else None,
+                                  "within_bound": int(np.sum((be <= bound) & (st == c)))}
+                             for c, nm in ((0, "cap"), (1, "converged"), (2, "stagnated"))}}}
     # the per-polynomial launch loop on a degree-stratified sample of the polynomials
     # the batched solve finished within loop_max_sweeps sweeps (bounded time)
     cand = np.where(it <= loop_max_sweeps)[0]

@@ -408,11 +408,13 @@ __global__ void __launch_bounds__(32 * DCOEF_WARPS)
     const int64_t n = coef_off[b + 1] - off - 1;
     if (n < 0) return;
     const int64_t base = b * npts;  // this polynomial's points
-    // On the FP64 pipe: at one warp per polynomial the adjoint workload keeps too
-    // few warps per SM to hide the hybrid engine's integer latency (hybrid: 632 ms,
-    // FP64 pipe: 538 ms = 88% of the pipe bound, same bits).  The restart path
-    // serves engines that can fail.
-    NativeEngine<typename P::T> g;
+    // The wavefront is bound by the FP64 pipe (one QD multiply-add per lane and
+    // step), so it runs on the hybrid engine for binary64 components, in the form
+    // that also packs subnormal error terms: the running powers dy x^i of points
+    // with |x| < 1 fall through the bottom of the binary64 range at high i, and
+    // with the default engine every polynomial holding such a point restarted on
+    // the FP64 pipe.  Any other failure restarts the polynomial there.
+    typename std::conditional<P::fp64, HybridEngine<false, false, true>, NativeEngine<typename P::T>>::type g;
     if (dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, g)) {
         NativeEngine<typename P::T> nat;
         dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, nat);

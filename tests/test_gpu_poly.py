@@ -85,9 +85,9 @@ def test_polyeval_backward_bit_exact(mp, oracle, prec, npts, dmax):
 @pytest.mark.parametrize("prec", ["dd", "td", "qd"])
 def test_horner_range_limits_bit_exact(mp, oracle, prec):
     """Points and adjoint seeds near the bottom of the binary64 range send the
-    hybrid engine to its FP64 recomputation (per point for values and dx, per
-    polynomial for the coefficient wavefront); every result stays bit-identical
-    to the oracle."""
+    default hybrid engine to its FP64 recomputation (per point for values and
+    dx); the coefficient wavefront's engine packs the subnormal error terms
+    itself.  Every result stays bit-identical to the oracle."""
     K, dt = oracle.PRECS[prec]
     off, coef = ragged(8, 6, 0, 70, K, dt)
     npoly, npts = len(off) - 1, 40
@@ -100,6 +100,25 @@ def test_horner_range_limits_bit_exact(mp, oracle, prec):
     dc, dx = mp.polyeval_backward(prec, doff, dcoef, npts, dev(x), dev(dy))
     wc, wx = oracle.polyeval_backward(prec, off, coef, npts, x, dy)
     assert same_bits(host(dc), wc) and same_bits(host(dx), wx)
+
+
+@pytest.mark.parametrize("prec", ["dd", "qd"])
+def test_dcoef_restart_on_fp64_pipe_bit_exact(mp, oracle, prec):
+    """One adjoint seed of 1.5 * 2^1023 puts TwoSum operands of the coefficient
+    wavefront above the hybrid engine's exponent bound: that polynomial restarts
+    on the FP64 pipe from its first pass, and the coefficient gradient equals
+    the oracle's bit for bit (points in [0, 1), so no running power overflows)."""
+    K, dt = oracle.PRECS[prec]
+    off, coef = ragged(8, 6, 0, 70, K, dt)
+    npoly, npts = len(off) - 1, 40
+    x = np.abs(inputs.mp_uniform(9, npoly * npts, K, dt, stream=inputs.STREAM_X))
+    dy = inputs.mp_uniform(10, npoly * npts, K, dt, stream=inputs.STREAM_Y)
+    dy[:, 2 * npts + 5] = 0.0
+    dy[0, 2 * npts + 5] = 1.5 * 2.0 ** 1023
+    dc, _ = mp.polyeval_backward(prec, dev(off), dev(coef), npts, dev(x), dev(dy), want_dx=False)
+    wc, _ = oracle.polyeval_backward(prec, off, coef, npts, x, dy, want_dx=False)
+    assert np.isfinite(wc).all()
+    assert same_bits(host(dc), wc)
 
 
 def test_polyeval_backward_workspace_checked(mp, oracle):
