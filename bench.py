@@ -1126,13 +1126,15 @@ def profile_one(a):
     if a.profile == "gemm":
         A, B = make_inputs(prec, a.n, a.seed)
         mpg.gemm(prec, dev(A), dev(B), config=a.gemm_config)
-    elif a.profile in ("horner", "dcoef"):
+    elif a.profile in ("horner", "estrin", "dcoef"):
         npoly, deg, npts = a.n, 256, 4096
         off = torch.arange(0, (npoly + 1) * (deg + 1), deg + 1, dtype=torch.int64, device="cuda")
         coef = dev(inputs.mp_uniform(4, npoly * (deg + 1), K, stream=inputs.STREAM_C))
         xs = dev(inputs.mp_uniform(5, npoly * npts, K, stream=inputs.STREAM_X))
         if a.profile == "horner":
             mpg.polyeval(prec, off, coef, npts, xs)
+        elif a.profile == "estrin":
+            mpg.polyeval(prec, off, coef, npts, xs, scheme="estrin")
         else:
             mpg.polyeval_backward(prec, off, coef, npts, xs, xs, want_dx=False)
     elif a.profile == "peak":
@@ -1325,7 +1327,7 @@ def main(argv=None):
                          "1 hybrid, 2 FP64 pipe")
     ap.add_argument("--dk-degree", type=int, default=0,
                     help="--profile dk: give every polynomial this degree (0: degrees uniform in [10, 500])")
-    ap.add_argument("--profile", choices=["gemm", "horner", "dcoef", "dk", "peak"], default=None,
+    ap.add_argument("--profile", choices=["gemm", "horner", "estrin", "dcoef", "dk", "peak"], default=None,
                     help="run one launch of this kernel family at size --n (for ncu) and exit")
     a = ap.parse_args(argv)
     if a.profile:
