@@ -247,7 +247,12 @@ __global__ void __launch_bounds__(256) k_polyeval_estrin(int64_t npoly, const in
         } else if (n >= 0) {
             const V zr = vload<P>(xr, px, idx);
             const V zi = CPLX ? vload<P>(xi, px, idx) : vzero<P>();
-            FastEngine<P> g;
+            // The powers x^(2^k) of points with |x| < 1 reach the bottom of the
+            // binary64 range (x^256 for |x| < 0.1 in QD), so the hybrid engine
+            // here also packs subnormal TwoSum error terms; with the default one
+            // every such point was recomputed on the FP64 pipe by a few lanes of
+            // its warp (ncu: 41% lane efficiency on the FP64 pipe, 2.9x Horner).
+            typename std::conditional<P::fp64, HybridEngine<false, false, true>, NativeEngine<typename P::T>>::type g;
             estrin_point<P, CPLX>(n, coef + off, pc, zr, zi, hr, hi, g);
             if (g.failed()) {
                 NativeEngine<typename P::T> nat;
