@@ -225,11 +225,12 @@ __device__ void block_max2(DKShared &sh, double a, double b, int bad)
     __syncthreads();
 }
 
-// The hybrid engine of the solver packs subnormal TwoSum error terms too: the
-// imaginary parts of iterates converging to real roots fall through the bottom
-// of the binary64 range within a few sweeps, and with the default engine every
-// such root was recomputed on the FP64 pipe (about 46,000 roots per sweep of the
-// batched workload, each a full update run by a few lanes of a warp).
+// The hybrid engine of the solver packs subnormal TwoSum error terms too: from
+// the second sweep on, some updates meet operands whose lower components fall
+// through the bottom of the binary64 range (imaginary parts of iterates that
+// converge to real roots, for one), and with the default engine every such root
+// was recomputed on the FP64 pipe (about 46,000 roots per sweep of the batched
+// workload, each a full update run by a few lanes of a warp).
 using DKHybrid = HybridEngine<false, false, true>;
 
 // Roots recomputed on the FP64 pipe because the hybrid engine left its domain
