@@ -250,6 +250,27 @@ def _oracle_row_rates(_=None):
     its = res["r"][1]
     out["durand_kerner"] = {"root_sweeps_per_s": float(np.sum(sub.degrees * its)) / t,
                             "sample": f"degrees {sub.degrees.tolist()}, 2 sweeps"}
+    # Table 4's standard / BF ratio on one host core (the paper's non-SIMD column):
+    # the oracle's GEMM at n = 96, conventional against branch-free
+    ng = 96
+    ratios = {}
+    for bf, nb in (("dd", "ddc"), ("td", "tdc"), ("qd", "qdc")):
+        Kb = o.PRECS[bf][0]
+        Ag = inputs.mp_uniform(2, (ng, ng), Kb, stream=inputs.STREAM_A)
+        Bg = inputs.mp_uniform(2, (ng, ng), Kb, stream=inputs.STREAM_B)
+        tb = timed(lambda: o.gemm(bf, Ag, Bg))
+        tn = timed(lambda: o.gemm(nb, Ag, Bg))
+        ratios[bf.upper()] = {f"{bf}_s": tb, f"{nb}_s": tn, "standard_over_bf": tn / tb}
+    out["bf_over_nobf"] = {**ratios, "sample": f"GEMM n = {ng}, one core, the oracle (scalar C, no SIMD)"}
+    # Eq. 1 at n = 2049: rows of the classical QD product
+    n1, rows = 2049, 4
+    s5, s3, tq, ia, ib = inputs.eq1_factors(n1, K)
+    r5 = o.mul("qd", np.repeat(s5[:, None], 2 * n1, 1), tq)
+    r3 = o.mul("qd", np.repeat(s3[:, None], 2 * n1, 1), tq)
+    A1 = np.ascontiguousarray(r5[:, ia[:rows]])
+    B1 = np.ascontiguousarray(r3[:, ib])
+    t = timed(lambda: o.gemm("qd", A1, B1))
+    out["eq1_n2049"] = {"qd_ops_per_s": 2.0 * rows * n1 * n1 / t, "sample": f"{rows} rows of the QD classical product"}
     # the paper's DK problem (Chebyshev, n = 64): one whole solve
     cq = inputs.rational_to_mp(inputs.chebyshev_quadrature(64), K)
     res = {}
@@ -315,6 +336,14 @@ def cpu_baseline_rows(pool, ex):
         put("gemm_strassen", "classical_equiv_qd_ops_per_s", best)
     if "durand_kerner" in ex:
         put("durand_kerner", "root_sweeps_per_s", ex["durand_kerner"]["root_sweeps_per_s"])
+    if "eq1_n2049" in ex and "qd" in ex["eq1_n2049"]:
+        put("eq1_n2049", "qd_ops_per_s", 2.0 * ex["eq1_n2049"]["n"] ** 3 / ex["eq1_n2049"]["qd"]["classical"]["s"])
+    if "bf_over_nobf" in ex and "bf_over_nobf" in o:
+        for key in ("DD", "TD", "QD"):
+            g = ex["bf_over_nobf"].get(key, {})
+            gpu = [v["standard_over_bf"] for k, v in g.items() if k.endswith("_fp64")]
+            if gpu:
+                o["bf_over_nobf"][key]["gpu_standard_over_bf_fp64_engine"] = gpu[-1]
     if "chebyshev_dk" in ex and "chebyshev_dk" in o:
         g, oc = ex["chebyshev_dk"], o["chebyshev_dk"]
         oc["gpu_single_solve_s"] = g["single_solve_gpu_s"]

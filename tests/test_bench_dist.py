@@ -69,12 +69,19 @@ def test_cpu_baseline_rows_beside_gpu_rows():
               "complex_gemm_3m": {"complex_qd_ops_per_s": 1.28e10},
               "gemm_strassen": {"n4096_cutoff2048": {"classical_equiv_qd_ops_per_s": 1.25e10}},
               "durand_kerner": {"root_sweeps_per_s": 1.3e6},
-              "chebyshev_dk": {"single_solve_gpu_s": 0.33, "precision": "qd", "sweeps": 230}}
+              "chebyshev_dk": {"single_solve_gpu_s": 0.33, "precision": "qd", "sweeps": 230},
+              "eq1_n2049": {"n": 2049, "qd": {"classical": {"s": 1.76}}},
+              "bf_over_nobf": {k: {"n2048_fp64": {"standard_over_bf": r}}
+                               for k, r in (("DD", 0.69), ("TD", 1.54), ("QD", 1.31))}}
         rows = bench.cpu_baseline_rows(pool, ex)
     finally:
         pool.close()
     assert set(rows) == set(ex)
     for key, r in rows.items():
+        if key == "bf_over_nobf":  # ratios on both sides, no throughput quotient
+            assert r["sample"] and all(r[p]["standard_over_bf"] > 0 and r[p]["gpu_standard_over_bf_fp64_engine"] > 0
+                                       for p in ("DD", "TD", "QD"))
+            continue
         assert r["sample"] and r["gpu_over_oracle"] > 0, key
     assert rows["axpy"]["gpu_elements_per_s"] == (1 << 24) / 3.2e-3
     # the Chebyshev ratio compares equal work: the oracle's solve took the GPU's 230 sweeps
