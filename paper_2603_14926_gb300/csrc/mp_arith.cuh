@@ -350,8 +350,11 @@ __device__ __forceinline__ mpv<T, 4> qw_mul_bf(const mpv<T, 4> &A, const mpv<T, 
 // exactly like an IEEE compare but issues on the integer pipe.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
-__device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+__device__ __forceinline__ bool nonzero(float x) { return (__float_as_uint(x) << 1) != 0u; }
 
 // TWRenormalize of (x0, x1, x2, x3): a bottom-up sweep of QuickTwoSums, then a
 // top-down one that opens a new component wherever an error term is nonzero
