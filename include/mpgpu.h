@@ -323,8 +323,13 @@ mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off
 /* when max_iter sweeps ran; 3 when the device watchdog (watchdog_cycles > 0,*/
 /* a clock64 budget per polynomial) stopped it.  Results, iteration counts  */
 /* and statuses are bit-identical to the CPU oracle and identical between   */
-/* the persistent batched launch (mode 0) and one launch per polynomial     */
-/* (mode 1), and between the engines: the hybrid engine (opts->engine 0 =   */
+/* the persistent batched launch (mode 0), one launch per polynomial        */
+/* (mode 1) and the cluster solve (mode 2: one thread-block cluster of      */
+/* C = max(2, ceil(max_degree/32)) <= 8 CTAs per polynomial, each CTA owning */
+/* ceil(n/C) roots, every complex step split over a lane pair, the new      */
+/* iterate exchanged through distributed shared memory once per sweep; for  */
+/* the latency of few polynomials; max_degree <= 256 and sort = 0, else     */
+/* MP_EINVAL), and between the engines: the hybrid engine (opts->engine 0 = */
 /* automatic, or 1) runs each root's update with TwoSum error terms on the  */
 /* integer pipes (see GEMM), the multicomponent add and multiply called out */
 /* of line; a root whose integer path leaves its domain is recomputed on the*/
@@ -344,7 +349,9 @@ typedef struct {
     int32_t max_iter;        /* <= 0: 1000 */
     int32_t stag_window;     /* <= 0: 5 */
     int32_t stag_min_iter;   /* <= 0: 10 */
-    int32_t mode;            /* 0: persistent batched launch, 1: one launch per polynomial */
+    int32_t mode;            /* 0: persistent batched launch, 1: one launch per polynomial,
+                                2: cluster solve (one thread-block cluster of 2-8 CTAs per
+                                polynomial, for latency; max_degree <= 256, sort = 0) */
     double radius;           /* > 0: start circle radius instead of Eq. 5's */
     int64_t watchdog_cycles; /* > 0: per-polynomial clock64 budget, status 3 when spent */
     int32_t max_degree;      /* host bound on every degree, required */

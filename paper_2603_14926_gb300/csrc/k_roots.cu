@@ -27,6 +27,7 @@
 // the stopping rule, the extended exponent of q and of the product, and the
 // starting values.  There are no inter-block waits; the optional watchdog is a
 // per-polynomial clock64 budget that ends the iteration with status 3.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "mp_arith.cuh"
@@ -388,29 +389,16 @@ __device__ __noinline__ void dk_update_native(int64_t i, int64_t n, const double
     dk_update<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi, nat);
 }
 
-template <class P, class E>
-__device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *smem)
+// Set-up of one polynomial's solve, by every thread of the block: monic
+// coefficients into c (K planes, stride cap) and the starting values into z
+// (2K planes, stride zc).
+template <class P>
+__device__ void dk_setup(const DKArgs<P> &A, int64_t n, int64_t off, int64_t ro, double *c, int64_t cap, double *z,
+                         int64_t zc, DKShared &sh)
 {
     using V = typename P::V;
     constexpr int K = P::K;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t off = A.coef_off[b];
-    const int64_t n = A.coef_off[b + 1] - off - 1;
-    const int64_t ro = off - b;  // root offset
-    if (n <= 0 || n > A.max_degree) {
-        if (tid == 0 && A.iters) {
-            A.iters[b] = 0;
-            A.status[b] = n <= 0 ? DK_CONVERGED : DK_BREAKDOWN;
-        }
-        return;
-    }
-    const int64_t cap = (int64_t)A.max_degree + 1;  // coefficient plane stride
-    const int64_t zc = A.max_degree;                // iterate plane stride
-    double *c = smem;                               // K planes
-    double *z = c + K * cap;                        // 2K planes: current iterate
-    double *zn = A.roots + ro;                      // 2K planes, stride proots: next iterate
-    const int64_t pn = A.proots;
-
     for (int64_t i = tid; i <= n; i += nt)
         for (int cc = 0; cc < K; cc++) c[cc * cap + i] = A.coef[cc * A.pcoef + off + i];
     __syncthreads();
@@ -470,6 +458,32 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
         }
     }
     __syncthreads();
+}
+
+template <class P, class E>
+__device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *smem)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t off = A.coef_off[b];
+    const int64_t n = A.coef_off[b + 1] - off - 1;
+    const int64_t ro = off - b;  // root offset
+    if (n <= 0 || n > A.max_degree) {
+        if (tid == 0 && A.iters) {
+            A.iters[b] = 0;
+            A.status[b] = n <= 0 ? DK_CONVERGED : DK_BREAKDOWN;
+        }
+        return;
+    }
+    const int64_t cap = (int64_t)A.max_degree + 1;  // coefficient plane stride
+    const int64_t zc = A.max_degree;                // iterate plane stride
+    double *c = smem;                               // K planes
+    double *z = c + K * cap;                        // 2K planes: current iterate
+    double *zn = A.roots + ro;                      // 2K planes, stride proots: next iterate
+    const int64_t pn = A.proots;
+
+    dk_setup<P>(A, n, off, ro, c, cap, z, zc, sh);
 
     const bool split = nt % 64 == 0 && n <= nt / 2 && n <= DK_SPLIT_MAX;
     // Product chains of a split sweep start 64 threads (two warps) after the Horner
@@ -621,6 +635,241 @@ __global__ void __launch_bounds__(256, DKLaunch<E>::min_blocks) k_dk_single(DKAr
     dk_solve<P, E>(A, A.order ? A.order[p] : p, sh, dk_smem);
 }
 
+// ---------------------------------------------------------------------------
+// Cluster solve (mode 2): one polynomial per thread-block cluster of C CTAs on
+// C SMs, for latency (one or a few polynomials of degree <= 32 C).  A single
+// block is bound by its SM's FP64 pipe; here CTA r owns roots r m .. r m + m - 1
+// (m = ceil(n / C)) and every complex step of a root's two recurrences is split
+// over a lane pair: the even lane forms the real part, the odd lane the
+// imaginary part, each with the same two products and add(s) in the same order
+// as the one-lane step, and the pair swaps its halves by shuffle.  So each
+// root's Horner value, product and update are bit-identical to the one-block
+// solver's.  Each CTA holds the coefficients and the whole current iterate in
+// shared memory; after a sweep every CTA writes its new roots into every CTA's
+// next-iterate buffer and its (delta, zmax, flags) into every CTA's slot
+// array through distributed shared memory, then one cluster barrier (release /
+// acquire) publishes them, and every CTA takes the same decision from the same
+// exact maxima.  Buffers alternate with the sweep's parity, so a CTA that runs
+// ahead never overwrites what another still reads.
+// ---------------------------------------------------------------------------
+
+constexpr int DK_CLUSTER_THREADS = 128;  // two Horner and two product warps at m = 32
+constexpr int DK_CLUSTER_MAX = 8;        // portable cluster size: degrees <= 256
+
+template <class P> __device__ __forceinline__ typename P::V pair_swap(const typename P::V &v)
+{
+    typename P::V r;
+#pragma unroll
+    for (int c = 0; c < P::K; c++) r.c[c] = __shfl_xor_sync(0xffffffffu, v.c[c], 1);
+    return r;
+}
+
+// Horner step of q(z_i) on coefficient kk, split over a lane pair (im = 0: real
+// part, 1: imaginary part).  One-lane form: t1 = hr zr, t2 = hi zi,
+// hr' = (t1 - t2) + a; t3 = hr zi, t4 = hi zr, hi' = t3 + t4.
+template <class P, class E>
+__device__ __forceinline__ void dk_horner_pair(const double *c, int64_t cap, int64_t kk, const typename P::V &zr,
+                                               const typename P::V &zi, typename P::V &hr, typename P::V &hi,
+                                               long long &Eq, int im, E &g)
+{
+    using V = typename P::V;
+    V a = vload<P>(c, cap, kk);
+    if (Eq > 1000) a = vzero<P>();
+    else if (Eq > 0) vscale<P>(a, (int)-Eq);
+    const V u = P::mul(hr, im ? zi : zr, g);
+    const V v = P::mul(hi, im ? zr : zi, g);
+    V w = P::add(u, im ? v : vneg<P>(v), g);
+    if (!im) w = P::add(w, a, g);
+    const V o = pair_swap<P>(w);
+    hr = im ? o : w;
+    hi = im ? w : o;
+    const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(hr, -DK_RESCALE);
+        vscale<P>(hi, -DK_RESCALE);
+        Eq += DK_RESCALE;
+    }
+}
+
+// Product step (z_i - z_j) split over a lane pair: each lane forms one part of
+// the difference, the pair swaps them, then each lane forms one part of the
+// complex product in cmul's order (re = t1 - t2, im = t3 + t4).  `take` false
+// (j == i) computes the same instructions and keeps the old product, so every
+// lane of the warp reaches every shuffle.
+template <class P, class E>
+__device__ __forceinline__ void dk_product_pair(const double *z, int64_t zc, int64_t j, bool take, const typename P::V &zr,
+                                                const typename P::V &zi, typename P::V &dr, typename P::V &di,
+                                                long long &Ed, int im, E &g)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    const uint32_t bad0 = g.bad_flags();
+    const V d = vsub<P>(im ? zi : zr, vload<P>(z + (im ? K * zc : 0), zc, j), g);
+    const V od = pair_swap<P>(d);
+    const V tr = im ? od : d, ti = im ? d : od;
+    const V u = P::mul(dr, im ? ti : tr, g);
+    const V v = P::mul(di, im ? tr : ti, g);
+    const V w = P::add(u, im ? v : vneg<P>(v), g);
+    const V o = pair_swap<P>(w);
+    V nr = im ? o : w, ni = im ? w : o;
+    long long nE = Ed;
+    const int be = max(bexp(nr.c[0]), bexp(ni.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(nr, -DK_RESCALE);
+        vscale<P>(ni, -DK_RESCALE);
+        nE += DK_RESCALE;
+    } else if (be <= 1023 - DK_RESCALE - 1 && (nr.c[0] != 0.0 || ni.c[0] != 0.0)) {
+        vscale<P>(nr, DK_RESCALE);
+        vscale<P>(ni, DK_RESCALE);
+        nE -= DK_RESCALE;
+    }
+    if (take) {
+        dr = nr;
+        di = ni;
+        Ed = nE;
+    } else {
+        g.set_bad_flags(bad0);
+    }
+}
+
+template <class P, class E>
+__global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
+{
+    namespace cg = cooperative_groups;
+    using V = typename P::V;
+    constexpr int K = P::K;
+    using PU = typename std::conditional<std::is_same<E, DKHybrid>::value, OutlinedHybrid<P>, P>::type;
+    extern __shared__ __align__(16) double dk_smem[];
+    __shared__ DKShared sh;
+    __shared__ double slot[2][DK_CLUSTER_MAX][4];  // per sweep parity and CTA: delta, zmax, bad, stop
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.x / C;
+    const int64_t off = A.coef_off[b];
+    const int64_t n = A.coef_off[b + 1] - off - 1;
+    const int64_t ro = off - b;
+    if (n <= 0 || n > A.max_degree) {  // the same for every CTA of the cluster: no barrier is reached
+        if (rank == 0 && tid == 0) {
+            A.iters[b] = 0;
+            A.status[b] = n <= 0 ? DK_CONVERGED : DK_BREAKDOWN;
+        }
+        return;
+    }
+    const int64_t cap = (int64_t)A.max_degree + 1, zc = A.max_degree;
+    const int64_t m = (n + C - 1) / C;                  // roots per CTA (<= 32)
+    double *c = dk_smem;                                // K planes
+    double *zbuf[2] = {c + K * cap, c + K * cap + 2 * K * zc};  // 2K planes each
+    double *pbuf = c + K * cap + 4 * K * zc;            // 2K planes of m: the products
+    long long *pE = reinterpret_cast<long long *>(pbuf + 2 * K * m);
+    int *pbad = reinterpret_cast<int *>(pE + m);
+
+    dk_setup<P>(A, n, off, ro, c, cap, zbuf[0], zc, sh);
+    cluster.sync();  // every CTA of the cluster runs before any remote write
+
+    const int64_t r0 = (int64_t)rank * m;
+    const int64_t cnt = n - r0 < m ? (n - r0 > 0 ? n - r0 : 0) : m;  // roots this CTA owns
+    const int hw = (int)((2 * m + 31) / 32);            // warps of Horner pairs, then as many of product pairs
+    const int warp = tid >> 5, im = tid & 1;
+    const bool horner = warp < hw, prod = !horner && warp < 2 * hw;
+    const int64_t q = horner ? tid / 2 : (tid - 32 * hw) / 2;   // pair index within the CTA
+    const bool valid = (horner || prod) && q < cnt;
+    const int64_t i = cnt > 0 ? r0 + (q < cnt ? q : cnt - 1) : 0;  // ghost pairs repeat a valid root
+
+    const long long t0 = clock64();
+    int st = DK_CAP, it = A.max_iter;
+    double best = __longlong_as_double(0x7ff0000000000000LL);
+    int since = 0;
+    for (int k = 1; k <= A.max_iter; k++) {
+        const int par = (k - 1) & 1;
+        double *z = zbuf[par], *zn = zbuf[par ^ 1];
+        const V zr = vload<P>(z, zc, i), zi = vload<P>(z + K * zc, zc, i);
+        V hr = vzero<P>(), hi = vzero<P>();
+        long long Eq = 0;
+        uint32_t hbad = 0;
+        E g;
+        if (prod) {
+            V dr = vone<P>(), di = vzero<P>();
+            long long Ed = 0;
+            for (int64_t j = 0; j < n; j++) dk_product_pair<PU>(z, zc, j, j != i, zr, zi, dr, di, Ed, im, g);
+            const uint32_t fb = g.bad_flags() | __shfl_xor_sync(0xffffffffu, g.bad_flags(), 1);
+            if (valid && !im) {
+                vstore<P>(pbuf, m, q, dr);
+                vstore<P>(pbuf + K * m, m, q, di);
+                pE[q] = Ed;
+                pbad[q] = fb != 0;
+            }
+        } else if (horner) {
+            hr = vload<P>(c, cap, n);
+            for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_pair<PU>(c, cap, kk, zr, zi, hr, hi, Eq, im, g);
+            hbad = g.bad_flags() | __shfl_xor_sync(0xffffffffu, g.bad_flags(), 1);
+        }
+        __syncthreads();  // the products are in place
+        double dmax = 0.0, zm = 0.0;
+        int bad = 0;
+        if (horner && valid && !im) {
+            const V dr = vload<P>(pbuf, m, q), di = vload<P>(pbuf + K * m, m, q);
+            V yr, yi, wr, wi;
+            E gf;
+            dk_finish<PU>(hr, hi, Eq, dr, di, pE[q], zr, zi, yr, yi, wr, wi, gf);
+            if (gf.failed() || hbad || pbad[q]) {
+                atomicAdd(&mp_dk_fallbacks, 1ull);
+                dk_update_native<P>(i, n, c, cap, z, zc, zr, zi, yr, yi, wr, wi);
+            }
+            for (int r = 0; r < C; r++) {  // the new root into every CTA's next-iterate buffer
+                double *dst = cluster.map_shared_rank(zn, r);
+                vstore<P>(dst, zc, i, yr);
+                vstore<P>(dst + K * zc, zc, i, yi);
+            }
+            const double d = __dadd_rn(fabs(wr.c[0]), fabs(wi.c[0]));
+            const double mm = __dadd_rn(fabs(yr.c[0]), fabs(yi.c[0]));
+            if (!(d == d) || isinf(d) || !(mm == mm) || isinf(mm)) bad = 1;
+            dmax = d;
+            zm = mm;
+        }
+        block_max2(sh, dmax, zm, bad);
+        if (tid == 0) {
+            const double stop = (A.watchdog > 0 && rank == 0 && (clock64() - t0) > A.watchdog) ? 1.0 : 0.0;
+            for (int r = 0; r < C; r++) {
+                double *dst = cluster.map_shared_rank(&slot[par][rank][0], r);
+                dst[0] = sh.delta;
+                dst[1] = sh.zmax;
+                dst[2] = sh.bad ? 1.0 : 0.0;
+                dst[3] = stop;
+            }
+        }
+        cluster.sync();  // new iterate and every CTA's maxima visible everywhere
+        double delta = 0.0, zmax = 0.0;
+        bool anybad = false;
+        for (int r = 0; r < C; r++) {
+            delta = fmax(delta, slot[par][r][0]);
+            zmax = fmax(zmax, slot[par][r][1]);
+            anybad = anybad || slot[par][r][2] != 0.0;
+        }
+        const bool stop = slot[par][0][3] != 0.0;
+        const double scale = zmax > 1.0 ? zmax : 1.0;
+        if (anybad) { st = DK_BREAKDOWN; it = k; break; }
+        if (delta <= __dmul_rn(A.tol, scale)) { st = DK_CONVERGED; it = k; break; }
+        if (delta < best) { best = delta; since = 0; } else { since++; }
+        if (k >= A.kmin && since >= A.win && best <= __dmul_rn(pow2(-26 * K), scale)) {
+            st = DK_STAGNATED;
+            it = k;
+            break;
+        }
+        if (stop) { st = DK_TIMEOUT; it = k; break; }
+    }
+    // the newest iterate: the buffer the last sweep wrote (the start values when none ran)
+    double *zf = zbuf[it < 1 ? 0 : (it & 1)];
+    for (int64_t j = tid; j < cnt; j += blockDim.x)
+        for (int cc = 0; cc < 2 * K; cc++) A.roots[cc * A.proots + ro + r0 + j] = zf[cc * zc + r0 + j];
+    if (rank == 0 && tid == 0) {
+        A.iters[b] = it;
+        A.status[b] = st;
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // Descending-degree order (ties by index): order[rank(p)] = p.
 __global__ void k_dk_order(int64_t npoly, const int64_t *__restrict__ coef_off, int32_t *__restrict__ order)
 {
@@ -688,10 +937,46 @@ template <class P> static int32_t dk_max_degree()
 static size_t dk_ws(int64_t npoly) { return 256 + (size_t)(npoly > 0 ? npoly : 0) * sizeof(int32_t); }
 
 // The persistent batched launch (mode 0) or one launch per polynomial (mode 1).
+// Cluster size for a cluster solve: one CTA per 32 roots of the largest
+// degree, at least 2, at most DK_CLUSTER_MAX (0 when the degree is too large).
+static int dk_cluster_size(int32_t max_degree)
+{
+    const int c = (max_degree + 31) / 32;
+    if (c > DK_CLUSTER_MAX) return 0;
+    return c < 2 ? 2 : c;
+}
+
+template <class P> static size_t dk_cluster_smem(int32_t max_degree, int C)
+{
+    const size_t m = ((size_t)max_degree + C - 1) / C;
+    return sizeof(double) * ((size_t)P::K * (max_degree + 1) + 4 * (size_t)P::K * max_degree + 2 * (size_t)P::K * m) +
+           m * (sizeof(long long) + sizeof(int)) + 16;
+}
+
 template <class P, class E>
 static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npoly, int threads, size_t smem,
                         cudaStream_t st)
 {
+    if (o->mode == 2) {
+        const int C = dk_cluster_size(o->max_degree);
+        const size_t cs = dk_cluster_smem<P>(o->max_degree, C);
+        if (C == 0 || npoly * C > 0x7fffffff) return MP_EINVAL;
+        cudaError_t e = cudaFuncSetAttribute(k_dk_cluster<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(npoly * C), 1, 1);
+        cfg.blockDim = dim3(DK_CLUSTER_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = cs;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cuda_status(cudaLaunchKernelEx(&cfg, k_dk_cluster<P, E>, A));
+    }
     if (o->mode == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_dk_persistent<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -730,7 +1015,8 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
         status == nullptr || pcoef < 1 || proots < 1 || (z0 && pz0 < 1))
         return MP_EINVAL;
     if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
-    if (o->mode != 0 && o->mode != 1) return MP_EINVAL;
+    if (o->mode < 0 || o->mode > 2) return MP_EINVAL;
+    if (o->mode == 2 && (dk_cluster_size(o->max_degree) == 0 || o->sort)) return MP_EINVAL;
     if (o->engine < 0 || o->engine > 2) return MP_EINVAL;
     const bool hybrid = o->engine != 2;  // 0 = automatic: the hybrid engine
     const int threads = o->threads > 0 ? o->threads

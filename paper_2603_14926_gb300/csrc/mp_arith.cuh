@@ -101,6 +101,8 @@ template <typename T> struct NativeEngine {
     __device__ __forceinline__ T add(T a, T b) { return fpu<T>::add(a, b); }
     __device__ __forceinline__ T mul(T a, T b) { return fpu<T>::mul(a, b); }
     __device__ __forceinline__ bool failed() const { return false; }
+    __device__ __forceinline__ uint32_t bad_flags() const { return 0; }
+    __device__ __forceinline__ void set_bad_flags(uint32_t) {}
 };
 
 template <bool QTS, bool TP = false, bool SUB = false> struct HybridEngine {
@@ -143,6 +145,8 @@ template <bool QTS, bool TP = false, bool SUB = false> struct HybridEngine {
     __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     __device__ __forceinline__ bool failed() const { return bad != 0; }
+    __device__ __forceinline__ uint32_t bad_flags() const { return bad; }
+    __device__ __forceinline__ void set_bad_flags(uint32_t v) { bad = v; }
 };
 
 // A K-component number, component 0 leading.  Always held in registers.
