@@ -1014,8 +1014,10 @@ def roots_full_extra(prec="qd", npoly=4096, max_iter=1000, loop_polys=8, loop_ma
 
 def chebyshev_extra(prec="qd", n=64, copies=4096, engine=0):
     """The paper's Durand-Kerner problem (Section 4.2, Eq. 6, n = 64; Table 6): one solve
-    on the GPU (latency), a batch of `copies` identical problems in one persistent
-    launch (throughput); the oracle's single solve is timed in the CPU baseline."""
+    on the GPU (latency: one block, and the cluster solve over several SMs;
+    `single_solve_gpu_s` is the faster), a batch of `copies` identical problems in
+    one persistent launch (throughput); the oracle's single solve is timed in the
+    CPU baseline."""
     import torch
 
     import paper_2603_14926_gb300 as mpg
@@ -1042,8 +1044,21 @@ def chebyshev_extra(prec="qd", n=64, copies=4096, engine=0):
     e1.record()
     torch.cuda.synchronize()
     tb = e0.elapsed_time(e1) / 1e3
+    # the cluster solve (mode 2): the same problem over a thread-block cluster of SMs
+    mpg.roots(prec, off1, c1, n, mode=2, max_iter=2)
+    torch.cuda.synchronize()
+    e0.record()
+    rc, itc, stc = mpg.roots(prec, off1, c1, n, mode=2)
+    e1.record()
+    torch.cuda.synchronize()
+    tc = e0.elapsed_time(e1) / 1e3
+    cluster = {"single_solve_gpu_s": tc, "cluster_ctas": max(2, (n + 31) // 32),
+               "identical_bits": bool(torch.equal(rc.view(torch.int64), r.view(torch.int64)) and
+                                      torch.equal(itc, it) and torch.equal(stc, st)),
+               "speedup_over_one_block": t1 / tc}
     res = {"n": n, "precision": prec, "sweeps": int(it.cpu()[0]), "status": int(st.cpu()[0]),
-           "single_solve_gpu_s": t1, "batch_copies": copies, "batch_s": tb,
+           "single_solve_gpu_s": min(t1, tc), "single_solve_one_block_s": t1, "single_solve_cluster": cluster,
+           "batch_copies": copies, "batch_s": tb,
            "batch_solves_per_s": copies / tb,
            "batch_fp64_instr_frac": dk_instr(prec, np.full(copies, n), itb.cpu().numpy(), hybrid=engine != 2) /
            tb / (NOMINAL_FP64_TFLOPS * 1e12 / 2),
