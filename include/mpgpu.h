@@ -338,11 +338,18 @@ mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off
 /*            coef_off[b] - b + j, plane stride proots                       */
 /*   z0     : NULL or starting values in the same layout (plane stride pz0)  */
 /*   iters, status : DEVICE int32[npoly]                                     */
-/*   ws     : DEVICE workspace of mp_roots_workspace_P(npoly) bytes, 8-byte  */
-/*            aligned (its first word is the 64-bit work-queue counter)      */
+/*   ws     : DEVICE workspace of mp_roots_workspace_deg_P(npoly,            */
+/*            opts->max_degree) bytes, 8-byte aligned (its first word is the */
+/*            64-bit work-queue counter; no initialisation needed).  Up to   */
+/*            mp_roots_max_degree_P() (the shared-memory bound: QD 2421, TD  */
+/*            3228, DD 4843) this equals mp_roots_workspace_P(npoly); above  */
+/*            it each block keeps its coefficients and iterate in a slot of  */
+/*            the workspace (4 slots per SM, at most 3 K (max_degree + 1)    */
+/*            doubles each; the persistent grid is then capped at 4 blocks  */
+/*            per SM), same results, and modes 0 and 1 only.                 */
 /*   opts->max_degree : host upper bound of the degrees (> 0 required; the   */
 /*            kernel skips, with status 4, any polynomial above it); at most */
-/*            mp_roots_max_degree_P()                                        */
+/*            2^20                                                           */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double tol;              /* <= 0: 2^-(53K - 6) */
@@ -370,6 +377,7 @@ typedef struct {
                                 int64_t pcoef, double radius, int32_t max_degree, double *z, \
                                 int64_t pz, mp_stream stream);                               \
     size_t mp_roots_workspace_##P(int64_t npoly);                                           \
+    size_t mp_roots_workspace_deg_##P(int64_t npoly, int32_t max_degree);                   \
     int32_t mp_roots_max_degree_##P(void);                                                  \
     mp_status mp_roots_##P(int64_t npoly, const int64_t *coef_off, const double *coef,       \
                            int64_t pcoef, const double *z0, int64_t pz0, double *roots,      \

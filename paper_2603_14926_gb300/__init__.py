@@ -116,6 +116,9 @@ def _declare(L):
         f = getattr(L, f"mp_roots_workspace_{p}")
         f.argtypes = [_i64]
         f.restype = ctypes.c_size_t
+        f = getattr(L, f"mp_roots_workspace_deg_{p}")
+        f.argtypes = [_i64, _i32]
+        f.restype = ctypes.c_size_t
         getattr(L, f"mp_roots_max_degree_{p}").restype = _i32
         f = getattr(L, f"mp_roots_{p}")
         f.argtypes = [_i64, _vp, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _vp,
@@ -445,8 +448,12 @@ def roots_init(prec, coef_off, coef, max_degree, radius=0.0):
     return z[:, :total]
 
 
-def roots_workspace(prec, npoly):
-    return int(getattr(lib(), f"mp_roots_workspace_{prec}")(npoly))
+def roots_workspace(prec, npoly, max_degree=None):
+    """Workspace bytes of mp_roots_P for npoly polynomials (and, above the
+    shared-memory bound, degrees up to max_degree)."""
+    if max_degree is None:
+        return int(getattr(lib(), f"mp_roots_workspace_{prec}")(npoly))
+    return int(getattr(lib(), f"mp_roots_workspace_deg_{prec}")(npoly, int(max_degree)))
 
 
 def roots_max_degree(prec):
@@ -466,7 +473,7 @@ def roots(prec, coef_off, coef, max_degree, z0=None, tol=0.0, max_iter=0, stag_w
     r = t.zeros((2 * K, max(total, 1)), dtype=coef.dtype, device=dev) if out is None else out
     iters = t.zeros(npoly, dtype=t.int32, device=dev)
     status = t.zeros(npoly, dtype=t.int32, device=dev)
-    nb = roots_workspace(prec, npoly)
+    nb = roots_workspace(prec, npoly, max_degree)
     if ws is None:
         ws = t.empty(max(nb, 1), dtype=t.uint8, device=dev)
     o = RootsOpts(tol, max_iter, stag_window, stag_min_iter, mode, radius, watchdog_cycles,
@@ -504,7 +511,7 @@ class RootsGraph:
         self._r = t.zeros((2 * K, max(self.total, 1)), dtype=coef.dtype, device=dev)
         self.iters = t.zeros(self.npoly, dtype=t.int32, device=dev)
         self.status = t.zeros(self.npoly, dtype=t.int32, device=dev)
-        self.ws = t.empty(max(roots_workspace(prec, self.npoly), 1), dtype=t.uint8, device=dev)
+        self.ws = t.empty(max(roots_workspace(prec, self.npoly, max_degree), 1), dtype=t.uint8, device=dev)
         self.opts = RootsOpts(tol, max_iter, stag_window, stag_min_iter, 0, radius, watchdog_cycles,
                               int(max_degree), threads, blocks_per_sm, sort, engine)
         # one single-sweep launch outside capture loads the module and sets the

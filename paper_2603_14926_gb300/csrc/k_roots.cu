@@ -193,6 +193,8 @@ template <class P> struct DKArgs {
     int32_t max_degree;
     const int32_t *order;  // nullptr: natural order
     unsigned long long *counter;  // persistent work queue (64-bit: pops past the end never wrap)
+    double *gscratch;      // nullptr: coefficients and iterate in shared memory; else per-block slots
+    int64_t gstride;       // doubles per block slot of gscratch
 };
 
 // block-wide max of two doubles and OR of a flag; result in sh
@@ -478,8 +480,11 @@ __device__ void dk_solve(const DKArgs<P> &A, int64_t b, DKShared &sh, double *sm
     }
     const int64_t cap = (int64_t)A.max_degree + 1;  // coefficient plane stride
     const int64_t zc = A.max_degree;                // iterate plane stride
-    double *c = smem;                               // K planes
-    double *z = c + K * cap;                        // 2K planes: current iterate
+    // K planes of coefficients, then 2K planes of the current iterate: in shared
+    // memory, or (degrees above the shared-memory bound) in this block's slot of
+    // the caller's workspace, which only this block touches
+    double *c = A.gscratch ? A.gscratch + (int64_t)blockIdx.x * A.gstride : smem;
+    double *z = c + K * cap;
     double *zn = A.roots + ro;                      // 2K planes, stride proots: next iterate
     const int64_t pn = A.proots;
 
@@ -936,6 +941,26 @@ template <class P> static int32_t dk_max_degree()
 
 static size_t dk_ws(int64_t npoly) { return 256 + (size_t)(npoly > 0 ? npoly : 0) * sizeof(int32_t); }
 
+// Degrees above the shared-memory bound keep each block's coefficients and
+// iterate in a slot of the workspace (after the queue and the order array).
+// The persistent grid is capped at DK_GLOBAL_SLOTS_PER_SM blocks per SM.
+constexpr int DK_GLOBAL_SLOTS_PER_SM = 4;
+constexpr int32_t DK_GLOBAL_MAX_DEGREE = 1 << 20;
+
+template <class P> static int64_t dk_slot_doubles(int32_t max_degree)
+{
+    return (int64_t)P::K * ((int64_t)max_degree + 1) + 2 * (int64_t)P::K * max_degree;
+}
+
+static size_t dk_slots_offset(int64_t npoly) { return (dk_ws(npoly) + 255) / 256 * 256; }
+
+template <class P> static size_t dk_ws_deg(int64_t npoly, int32_t max_degree)
+{
+    if (max_degree <= dk_max_degree<P>()) return dk_ws(npoly);
+    const int64_t slots = (int64_t)sm_count() * DK_GLOBAL_SLOTS_PER_SM;
+    return dk_slots_offset(npoly) + (size_t)slots * (size_t)dk_slot_doubles<P>(max_degree) * sizeof(double);
+}
+
 // The persistent batched launch (mode 0) or one launch per polynomial (mode 1).
 // Cluster size for a cluster solve: one CTA per 32 roots of the largest
 // degree, at least 2, at most DK_CLUSTER_MAX (0 when the degree is too large).
@@ -987,6 +1012,7 @@ static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npol
             if (e != cudaSuccess) return cuda_status(e);
             if (per_sm < 1) per_sm = 1;
         }
+        if (A.gscratch && per_sm > DK_GLOBAL_SLOTS_PER_SM) per_sm = DK_GLOBAL_SLOTS_PER_SM;
         int64_t grid = (int64_t)sm_count() * per_sm;
         if (grid > npoly) grid = npoly;
         e = cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), st);
@@ -1014,7 +1040,8 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
     if (npoly > 0x7fffffff || coef_off == nullptr || coef == nullptr || roots == nullptr || iters == nullptr ||
         status == nullptr || pcoef < 1 || proots < 1 || (z0 && pz0 < 1))
         return MP_EINVAL;
-    if (o->max_degree <= 0 || o->max_degree > dk_max_degree<P>()) return MP_EINVAL;
+    if (o->max_degree <= 0 || o->max_degree > DK_GLOBAL_MAX_DEGREE) return MP_EINVAL;
+    const bool global = o->max_degree > dk_max_degree<P>();
     if (o->mode < 0 || o->mode > 2) return MP_EINVAL;
     if (o->mode == 2 && (dk_cluster_size(o->max_degree) == 0 || o->sort)) return MP_EINVAL;
     if (o->engine < 0 || o->engine > 2) return MP_EINVAL;
@@ -1025,7 +1052,7 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
     if (threads % 32 != 0 || threads > 256) return MP_EINVAL;
     if (o->sort && npoly > (1 << 16)) return MP_EINVAL;
     if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 8 != 0) return MP_EINVAL;
-    if (ws_bytes < dk_ws(npoly)) return MP_ENOMEM;
+    if (ws_bytes < dk_ws_deg<P>(npoly, o->max_degree)) return MP_ENOMEM;
     cudaStream_t st = as_stream(s);
     DKArgs<P> A{};
     A.npoly = npoly;
@@ -1048,7 +1075,9 @@ static mp_status roots_launch(int64_t npoly, const int64_t *coef_off, const doub
     A.counter = static_cast<unsigned long long *>(ws);
     int32_t *order = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + 256);
     A.order = nullptr;
-    const size_t smem = dk_smem_bytes<P>(o->max_degree);
+    A.gscratch = global ? reinterpret_cast<double *>(static_cast<char *>(ws) + dk_slots_offset(npoly)) : nullptr;
+    A.gstride = global ? dk_slot_doubles<P>(o->max_degree) : 0;
+    const size_t smem = global ? 0 : dk_smem_bytes<P>(o->max_degree);
     if (o->sort) {
         k_dk_order<<<grid_for(npoly, 256, 4), 256, 0, st>>>(npoly, coef_off, order);
         mp_status e = launch_status();
@@ -1083,6 +1112,11 @@ extern "C" {
 
 #define MP_EXPORT_ROOTS(S, PT)                                                                        \
     size_t mp_roots_workspace_##S(int64_t npoly) { return dk_ws(npoly); }                             \
+    size_t mp_roots_workspace_deg_##S(int64_t npoly, int32_t max_degree)                              \
+    {                                                                                                 \
+        if (npoly < 0 || max_degree <= 0 || max_degree > DK_GLOBAL_MAX_DEGREE) return 0;              \
+        return dk_ws_deg<PT>(npoly, max_degree);                                                      \
+    }                                                                                                 \
     int32_t mp_roots_max_degree_##S(void) { return dk_max_degree<PT>(); }                             \
     mp_status mp_roots_init_##S(int64_t npoly, const int64_t *coef_off, const double *coef,            \
                                 int64_t pcoef, double radius, int32_t max_degree, double *z, int64_t pz, \

@@ -285,7 +285,16 @@ def test_roots_watchdog_and_degree_bound(mp, oracle):
     assert np.all(st[prob.degrees > small] == mp.DK_BREAKDOWN)
     assert np.all(st[prob.degrees == small] != mp.DK_BREAKDOWN)
     with pytest.raises(mp.MPError, match="invalid"):
-        mp.roots(prec, dev(prob.coef_off), coef, mp.roots_max_degree(prec) + 1)
+        mp.roots(prec, dev(prob.coef_off), coef, (1 << 20) + 1)
+    with pytest.raises(mp.MPError, match="workspace"):  # above the shared-memory bound: slots needed
+        big = mp.roots_max_degree(prec) + 1
+        mp.roots(prec, dev(prob.coef_off), coef, big, ws=torch_empty(mp.roots_workspace(prec, prob.npoly)))
+
+
+def torch_empty(nbytes):
+    import torch
+
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
 
 
 def test_roots_batch_workload_sampled(mp, oracle):
