@@ -603,14 +603,13 @@ def extras(prec="qd", quick=False):
     te1 = timed(lambda: mpg.polyeval(prec, off1, c1, 64, x1, scheme="estrin"), reps=5)
     out["estrin_latency_one_poly_64_points"] = {"horner_ms": th1 * 1e3, "estrin_ms": te1 * 1e3,
                                                 "estrin_over_horner": te1 / th1}
-    wsb = torch.empty(mpg.polyeval_backward_workspace(prec, npoly, npts), dtype=torch.uint8, device="cuda")
-    tb = timed(lambda: mpg.polyeval_backward(prec, off, coef, npts, xs, dy, ws=wsb), reps=1)
+    tb = timed(lambda: mpg.polyeval_backward(prec, off, coef, npts, xs, dy), reps=1)
     # dx: 2 mul + 2 add per step (+1 mul), dcoef: 1 mul + 1 add per (coefficient, point),
     # both on the hybrid engine
     bw = lambda i, mu: steps * 2 * i + npoly * npts * mu + npoly * npts * (deg + 1) * i  # noqa: E731
     out["horner_bwd"] = {"ms": tb * 1e3, "vs_fwd": tb / t,
                          **rates(bw(ins, mul_instr(prec)), bw(ins_paper, INSTR_MUL[prec]), tb)}
-    del off, coef, xs, dy, wsb
+    del off, coef, xs, dy
     # GEMM adjoint through torch.autograd.Function: dA = dC B^T, dB = A^T dC
     from paper_2603_14926_gb300.autograd import mp_gemm
 

@@ -262,9 +262,9 @@ const char *mp_version(void);
 /*                 w_0 = dy, w_{i+1} = mul(w_i, x): the reverse sweep of Horner's*/
 /*                 recurrence h_i = h_{i+1} x + a_i.                             */
 /* Both are bit-identical to the CPU oracle.  Either output may be NULL.        */
-/* ws: DEVICE workspace of mp_polyeval_backward_workspace_P(npoly, npts) bytes   */
-/* (the running powers between blocks of 32 coefficients; needed only when      */
-/* dcoef != NULL, contents need no initialisation).                             */
+/* ws, ws_bytes: unused (may be NULL, 0); mp_polyeval_backward_workspace_P     */
+/* answers 0.  The coefficient sweep keeps its partial sums in dcoef itself, so */
+/* dcoef's contents are undefined while the call runs.                          */
 
 /* ------------------------------------------------------------------------ */
 /* mp_polyeval_backward_noalloc_qd: the QD Horner adjoint without a caller    */

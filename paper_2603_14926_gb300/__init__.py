@@ -409,7 +409,8 @@ def polyeval_backward_workspace(prec, npoly, npts):
 
 
 def polyeval_backward(prec, coef_off, coef, npts, x, dy, want_dcoef=True, want_dx=True, ws=None):
-    """Adjoint of real-argument polyeval: returns (dcoef, dx) (None where not wanted)."""
+    """Adjoint of real-argument polyeval: returns (dcoef, dx) (None where not wanted).
+    `ws` is accepted and unused: the adjoint needs no workspace."""
     t = _torch()
     _check(prec, coef, "coef", 2)
     _check(prec, x, "x", 2)

@@ -9,14 +9,12 @@
 // Adjoint, dy -> (dcoef, dx):
 //   dx: one thread per point, simultaneous Horner recurrence for p'.
 //   dcoef_i = sum over points m (ascending) of dy_m x_m^i.  One warp per
-//   polynomial sweeps the coefficients as a wavefront, DCOEF_DEPTH blocks of 32
-//   per pass: lane L owns coefficient i = j0 + 32d + L and at step s handles
-//   point m = s - 32d - L, receiving dy_m x_m^(i-1) * x_m from the coefficient
-//   before it (lane L-1, or lane 31 of block d-1) through a register shuffle.
-//   Each coefficient is therefore folded over the points in ascending order
-//   with the powers formed by repeated multiplication -- the oracle's order, so
-//   the result is bit-identical.  The last block's lane 31 hands the running
-//   powers of the next pass over through a per-point workspace.
+//   polynomial; lane L takes the points L, L+32, ... in turn and runs each
+//   point's powers dy_m x_m^i up the coefficients, while the partial sums S_i
+//   travel along the lanes (register shuffles) and from lane 31 back to lane 0
+//   through dcoef itself.  Each coefficient is folded over the points in
+//   ascending order with the powers formed by repeated multiplication -- the
+//   oracle's order, so the result is bit-identical.  No workspace.
 //
 // Polynomials from roots: one block per polynomial, the coefficient vector in
 // shared memory, one factor (x - r) or (x^2 + Bx + C) per synchronised stage,
@@ -25,10 +23,10 @@
 // Evaluation and dx run on FastEngine<P> (binary64: TwoSum's error term on the
 // integer pipes); a point whose integer path left its domain is recomputed
 // with the FP64 pipe, so every result is the FP64 sequence's bits.  The
-// coefficient wavefront runs on the FP64 pipe (see k_poly_dcoef); its sweep
-// routine also takes a failing engine, restarting the whole polynomial on the
-// FP64 pipe when any lane of the warp failed, because its lanes pass values to
-// each other and to the next pass.
+// coefficient sweep runs on the hybrid engine that also packs subnormal error
+// terms (see k_poly_dcoef); when any lane of the warp left its domain the whole
+// polynomial is redone on the FP64 pipe, because the lanes pass partial sums to
+// each other.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -336,101 +334,120 @@ __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *_
     }
 }
 
-constexpr int DCOEF_WARPS = 4;
+// Warps per block of the coefficient adjoint.  One warp per polynomial and one
+// warp per block: with 1024 polynomials the block scheduler then spreads 6 or 7
+// warps over each SM; four-warp blocks left some SMs twice the work of others
+// (245 ms against 270 ms on 1024 polynomials x degree 256 x 4096 points).
+constexpr int DCOEF_WARPS = 1;
 
-// Coefficient blocks per warp pass.  Lane L holds coefficients j0 + 32d + L for
-// d = 0..DCOEF_DEPTH-1; block d trails block d-1 by 32 points, so block d's lane 0
-// takes the running power from block d-1's lane 31 one step later through the
-// same rotation shuffle.  Depths 1-4 measured the same (537.6 ms on 1024
-// polynomials x degree 256 x 4096 points): the wavefront is FP64-pipe bound.
-constexpr int DCOEF_DEPTH = 1;
-
-// All coefficient passes of one polynomial (one warp).  Returns true, after the
-// pass in which it happened, when any lane's engine failed; the caller then
-// starts again from the first pass (dy is never overwritten) on the FP64 pipe.
+// The coefficient adjoint of one polynomial (one warp).  Lane L takes the points
+// m = 32g + L, g = 0, 1, ..., one after another, and spends Q = max(n + 1, 32)
+// steps on each: at local step i <= n it adds w_i = dy_m x_m^i to S_i, the fold
+// of w_i over the points before m, and forms w_{i+1} = w_i x_m (w_0 = dy_m).  That partial sum comes from lane L-1, which handled point
+// m - 1 at the same local step one step earlier (a register shuffle); lane 0
+// takes it from the group before, parked in dcoef_i by lane 31 Q - 31 >= 1
+// steps earlier (and overwritten by lane 31 only 31 steps after the read).
+// Points past npts pass the sum on unchanged, so lane 31's last write of each
+// S_i is the whole fold.  Every coefficient is folded over the points in
+// ascending order with the powers formed by repeated multiplication: the
+// oracle's order and operations, so the result is bit-identical.  Returns true
+// when any lane's engine failed; the caller then redoes the polynomial on the
+// FP64 pipe (dy and x are never overwritten, and nothing is read from dcoef
+// before it was written in the same sweep).
 template <class P, class E>
-__device__ __forceinline__ bool dcoef_sweeps(int64_t n, int64_t off, int64_t base, int64_t npts,
-                                             const typename P::T *__restrict__ x, int64_t px,
-                                             const typename P::T *__restrict__ dy, int64_t pdy,
-                                             typename P::T *__restrict__ dcoef, int64_t pdc,
-                                             typename P::T *__restrict__ wbuf, int64_t pw, E &g)
+__device__ __forceinline__ bool dcoef_ring(int64_t n, int64_t off, int64_t base, int64_t npts,
+                                           const typename P::T *__restrict__ x, int64_t px,
+                                           const typename P::T *__restrict__ dy, int64_t pdy,
+                                           typename P::T *dcoef, int64_t pdc, E &g)
 {
     using V = typename P::V;
-    constexpr int D = DCOEF_DEPTH;
     const int lane = threadIdx.x & 31;
-    for (int64_t j0 = 0; j0 <= n; j0 += 32 * D) {
-        V S[D], win[D];
-#pragma unroll
-        for (int d = 0; d < D; d++) S[d] = win[d] = vzero<P>();
-        const int64_t last = npts + 32 * D - 1;  // steps until the last block's lane 31 is done
-        for (int64_t s = 0; s < last; s++) {
-            V wout[D];
-#pragma unroll
-            for (int d = 0; d < D; d++) {
-                const int64_t i = j0 + 32 * d + lane, m = s - 32 * d - lane;
-                const bool act = m >= 0 && m < npts && i <= n;
-                V w = win[d];
-                if (d == 0 && lane == 0 && act) w = j0 == 0 ? vload<P>(dy, pdy, base + m) : vload<P>(wbuf, pw, base + m);
-                wout[d] = vzero<P>();
-                if (act) {
-                    S[d] = P::add(S[d], w, g);
-                    if (i < n) wout[d] = P::mul(w, vload<P>(x, px, base + m), g);
+    const int64_t Q = n + 1 > 32 ? n + 1 : 32;
+    const int64_t groups = (npts + 31) / 32;
+    const int64_t steps = groups * Q + 31;
+    int64_t i = -lane;  // local step within the current point (negative: not started)
+    int64_t m = lane;   // current point
+    bool have = false;  // m < npts
+    const V zero = vzero<P>();
+    V w = zero, xm = zero, carry = zero;
+    for (int64_t t = 0; t < steps; t++) {
+        V s = carry;  // lane L-1's partial sum from the step before
+        bool act = false;
+        if (i >= 0) {
+            if (i == 0) {
+                have = m < npts;
+                if (have) {
+                    xm = vload<P>(x, px, base + m);
+                    w = vload<P>(dy, pdy, base + m);  // w_0
                 }
-                if (d == D - 1 && lane == 31 && act && i < n) vstore<P>(wbuf, pw, base + m, wout[d]);
             }
-            // lane L receives lane L-1's outputs; lane 0 of block d takes block d-1's lane 31
-            V r[D];
+            act = have && i <= n;
+            if (lane == 0 && i <= n) {
+                if (m < 32) {
+                    s = zero;
+                } else {
 #pragma unroll
-            for (int d = 0; d < D; d++)
-#pragma unroll
-                for (int c = 0; c < P::K; c++) r[d].c[c] = __shfl_sync(0xffffffffu, wout[d].c[c], (lane + 31) & 31);
-#pragma unroll
-            for (int d = 0; d < D; d++) win[d] = lane == 0 ? (d > 0 ? r[d - 1] : vzero<P>()) : r[d];
+                    for (int c = 0; c < P::K; c++) s.c[c] = __ldcg(dcoef + c * pdc + off + i);
+                }
+            }
         }
-        if (__any_sync(0xffffffffu, g.failed())) return true;
+        // S_i += w_i and w_{i+1} = w_i x_m are independent: both are issued
+        // unconditionally (zero operands where a lane has nothing to do, so the
+        // engine sees no spurious operands) and their instructions interleave.
+        const bool nxt = act && i < n;
+        const V sum = P::add(act ? s : zero, act ? w : zero, g);
+        const V pw = P::mul(nxt ? w : zero, nxt ? xm : zero, g);
+        if (act) s = sum;
+        if (nxt) w = pw;
+        if (lane == 31 && i >= 0 && i <= n) {
 #pragma unroll
-        for (int d = 0; d < D; d++) {
-            const int64_t i = j0 + 32 * d + lane;
-            if (i <= n) vstore<P>(dcoef, pdc, off + i, S[d]);
+            for (int c = 0; c < P::K; c++) __stcg(dcoef + c * pdc + off + i, s.c[c]);
         }
-        __syncwarp();
+        __syncwarp();  // orders lane 31's write before lane 0's read Q - 31 steps later
+#pragma unroll
+        for (int c = 0; c < P::K; c++) carry.c[c] = __shfl_up_sync(0xffffffffu, s.c[c], 1);
+        if (++i == Q) {
+            i = 0;
+            m += 32;
+        }
     }
-    return false;
+    return __any_sync(0xffffffffu, g.failed());
 }
 
 template <class P>
 __global__ void __launch_bounds__(32 * DCOEF_WARPS)
     k_poly_dcoef(int64_t npoly, const int64_t *__restrict__ coef_off, int64_t npts,
                  const typename P::T *__restrict__ x, int64_t px, const typename P::T *__restrict__ dy,
-                 int64_t pdy, typename P::T *__restrict__ dcoef, int64_t pdc, typename P::T *__restrict__ wbuf,
-                 int64_t pw)
+                 int64_t pdy, typename P::T *dcoef, int64_t pdc)
 {
-    using V = typename P::V;
     const int lane = threadIdx.x & 31;
     const int64_t b = (int64_t)blockIdx.x * DCOEF_WARPS + (threadIdx.x >> 5);
     if (b >= npoly) return;  // whole warp
     const int64_t off = coef_off[b];
     const int64_t n = coef_off[b + 1] - off - 1;
     if (n < 0) return;
+    if (npts == 0) {  // an empty fold
+        for (int64_t i = lane; i <= n; i += 32) vstore<P>(dcoef, pdc, off + i, vzero<P>());
+        return;
+    }
     const int64_t base = b * npts;  // this polynomial's points
-    // The wavefront is bound by the FP64 pipe (one QD multiply-add per lane and
-    // step), so it runs on the hybrid engine for binary64 components, in the form
-    // that also packs subnormal error terms: the running powers dy x^i of points
-    // with |x| < 1 fall through the bottom of the binary64 range at high i, and
-    // with the default engine every polynomial holding such a point restarted on
-    // the FP64 pipe.  Any other failure restarts the polynomial there.
+    // The sweep is bound by the FP64 pipe (one QD multiply and one add per
+    // coefficient and point), so it runs on the hybrid engine for binary64
+    // components, in the form that also packs subnormal error terms: the running
+    // powers dy x^i of points with |x| < 1 fall through the bottom of the
+    // binary64 range at high i, and with the default engine every polynomial
+    // holding such a point restarted on the FP64 pipe.  Any other failure
+    // restarts the polynomial there.
     typename std::conditional<P::fp64, HybridEngine<false, false, true>, NativeEngine<typename P::T>>::type g;
-    if (dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, g)) {
+    if (dcoef_ring<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, g)) {
         NativeEngine<typename P::T> nat;
-        dcoef_sweeps<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, wbuf, pw, nat);
+        dcoef_ring<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, nat);
     }
 }
 
-template <class P> static size_t backward_ws(int64_t npoly, int64_t npts)
-{
-    if (npoly <= 0 || npts <= 0) return 0;
-    return (size_t)npoly * (size_t)npts * P::K * sizeof(typename P::T);
-}
+// The adjoint needs no workspace: the coefficient sweep parks its partial sums
+// in dcoef itself.  The size query stays in the interface and answers 0.
+template <class P> static size_t backward_ws(int64_t, int64_t) { return 0; }
 
 template <class P>
 static mp_status polyeval_backward_launch(int64_t npoly, const int64_t *coef_off, const typename P::T *coef,
@@ -447,7 +464,8 @@ static mp_status polyeval_backward_launch(int64_t npoly, const int64_t *coef_off
     // every argument check before the first launch: an error return enqueues nothing
     if (dx && total > 0 && pdx < total) return MP_EINVAL;
     if (dcoef && pdc < 1) return MP_EINVAL;
-    if (dcoef && total > 0 && (ws == nullptr || ws_bytes < backward_ws<P>(npoly, npts))) return MP_ENOMEM;
+    (void)ws;  // no workspace needed (backward_ws)
+    (void)ws_bytes;
     if (dx && total > 0) {
         k_poly_dx<P><<<grid_for(total, 256, 8), 256, 0, as_stream(s)>>>(npoly, coef_off, coef, pc, npts, x,
                                                                          px, dy, pdy, dx, pdx);
@@ -456,8 +474,8 @@ static mp_status polyeval_backward_launch(int64_t npoly, const int64_t *coef_off
     }
     if (dcoef) {
         const int64_t blocks = (npoly + DCOEF_WARPS - 1) / DCOEF_WARPS;
-        k_poly_dcoef<P><<<(unsigned)blocks, 32 * DCOEF_WARPS, 0, as_stream(s)>>>(
-            npoly, coef_off, npts, x, px, dy, pdy, dcoef, pdc, static_cast<typename P::T *>(ws), total);
+        k_poly_dcoef<P><<<(unsigned)blocks, 32 * DCOEF_WARPS, 0, as_stream(s)>>>(npoly, coef_off, npts, x, px,
+                                                                                 dy, pdy, dcoef, pdc);
         return launch_status();
     }
     return MP_OK;

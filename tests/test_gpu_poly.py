@@ -62,11 +62,13 @@ def test_polyeval_estrin_bit_exact(mp, oracle, prec):
 
 
 @pytest.mark.parametrize("prec", ["dd", "td", "qd", "qf"])
-@pytest.mark.parametrize("npts", [0, 1, 77])
+@pytest.mark.parametrize("npts", [0, 1, 64, 77])
 @pytest.mark.parametrize("dmax", [70, 200])
 def test_polyeval_backward_bit_exact(mp, oracle, prec, npts, dmax):
-    """Degrees 0..70 fit one pass of the wavefront (three blocks of 32 coefficients);
-    degrees up to 200 take three passes chained through the workspace."""
+    """Degrees 0..70 run the coefficient sweep with padded point periods (fewer
+    than 32 coefficients) and full ones; degrees 90..200 have more coefficients
+    than points.  64 points fill two groups of 32 exactly, 77 leave a ragged
+    last group, 1 a single lane, 0 an empty fold."""
     K, dt = oracle.PRECS[prec]
     off, coef = ragged(4, 7, 0 if dmax == 70 else 90, dmax, K, dt)
     off[2] = off[1]  # an empty polynomial (no coefficients)
@@ -86,7 +88,7 @@ def test_polyeval_backward_bit_exact(mp, oracle, prec, npts, dmax):
 def test_horner_range_limits_bit_exact(mp, oracle, prec):
     """Points and adjoint seeds near the bottom of the binary64 range send the
     default hybrid engine to its FP64 recomputation (per point for values and
-    dx); the coefficient wavefront's engine packs the subnormal error terms
+    dx); the coefficient sweep's engine packs the subnormal error terms
     itself.  Every result stays bit-identical to the oracle."""
     K, dt = oracle.PRECS[prec]
     off, coef = ragged(8, 6, 0, 70, K, dt)
@@ -105,8 +107,8 @@ def test_horner_range_limits_bit_exact(mp, oracle, prec):
 @pytest.mark.parametrize("prec", ["dd", "qd"])
 def test_dcoef_restart_on_fp64_pipe_bit_exact(mp, oracle, prec):
     """One adjoint seed of 1.5 * 2^1023 puts TwoSum operands of the coefficient
-    wavefront above the hybrid engine's exponent bound: that polynomial restarts
-    on the FP64 pipe from its first pass, and the coefficient gradient equals
+    sweep above the hybrid engine's exponent bound: that polynomial restarts
+    on the FP64 pipe from its first point, and the coefficient gradient equals
     the oracle's bit for bit (points in [0, 1), so no running power overflows)."""
     K, dt = oracle.PRECS[prec]
     off, coef = ragged(8, 6, 0, 70, K, dt)
@@ -121,18 +123,16 @@ def test_dcoef_restart_on_fp64_pipe_bit_exact(mp, oracle, prec):
     assert same_bits(host(dc), wc)
 
 
-def test_polyeval_backward_workspace_checked(mp, oracle):
-    import torch
-
+def test_polyeval_backward_needs_no_workspace(mp, oracle):
+    """The coefficient sweep keeps its partial sums in dcoef itself: the size
+    query answers 0 and a call without a workspace equals the oracle."""
     K, dt = 4, np.float64
-    off, coef = ragged(4, 3, 5, 9, K, dt)
-    x = dev(inputs.mp_uniform(5, 3 * 40, K, dt))
-    with pytest.raises(mp.MPError, match="workspace"):
-        mp.polyeval_backward("qd", dev(off), dev(coef), 40, x, x,
-                             ws=torch.empty(16, dtype=torch.uint8, device="cuda"))
-    # dx alone needs no workspace
-    _, dx = mp.polyeval_backward("qd", dev(off), dev(coef), 40, x, x, want_dcoef=False)
-    assert dx.shape == (4, 120)
+    off, coef = ragged(4, 3, 5, 40, K, dt)
+    x = inputs.mp_uniform(5, 3 * 40, K, dt)
+    assert mp.polyeval_backward_workspace("qd", 3, 40) == 0
+    dc, dx = mp.polyeval_backward("qd", dev(off), dev(coef), 40, dev(x), dev(x))
+    wc, wx = oracle.polyeval_backward("qd", off, coef, 40, x, x)
+    assert same_bits(host(dc), wc) and same_bits(host(dx), wx)
 
 
 @pytest.mark.parametrize("prec", ["dd", "ddc", "td", "qd"])
