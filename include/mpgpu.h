@@ -267,30 +267,6 @@ const char *mp_version(void);
 /* dcoef's contents are undefined while the call runs.                          */
 
 /* ------------------------------------------------------------------------ */
-/* mp_polyeval_backward_noalloc_qd: the QD Horner adjoint without a caller    */
-/* workspace, for code that cannot allocate device memory (a fixed memory     */
-/* pool that must not grow, a plugin whose allocator belongs to its host, a   */
-/* real-time loop where an allocation could stall).  The paper has no         */
-/* counterpart; this is a library convenience.  Same arguments and same       */
-/* results (bit for bit) as mp_polyeval_backward_qd without ws/ws_bytes.  Its  */
-/* scratch is a fixed 4 MiB device array inside the library, held by every GPU */
-/* that loads the library until the process exits, so dcoef requests need     */
-/* npoly * npts <= MP_NOALLOC_MAX_POINTS (131072 points); larger ones return  */
-/* MP_ENOMEM before anything is enqueued (dx-only calls have no limit).  The   */
-/* first call on a device looks the array up (cudaGetSymbolAddress) for that  */
-/* device, so make it before any stream capture.  Concurrent calls from host */
-/* threads are safe on the host side (the lookup is guarded), but calls share */
-/* the array: calls whose kernels overlap on the GPU race on it.  It needs no */
-/* initialisation between calls.  After cudaDeviceReset on a device, do not  */
-/* call it on that device again (the looked-up address is kept).             */
-/* ------------------------------------------------------------------------ */
-#define MP_NOALLOC_MAX_POINTS (1 << 17)
-mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef,
-                                          int64_t pcoef, int64_t npts, const double *x, int64_t px,
-                                          const double *dy, int64_t pdy, double *dcoef, int64_t pdc,
-                                          double *dx, int64_t pdx, mp_stream stream);
-
-/* ------------------------------------------------------------------------ */
 /* POLY_FROM_ROOTS: coefficients of prod (x - r) (the root-solving workload): */
 /* per polynomial, rootdata holds floor(n/2) complex roots as (re, im)      */
 /* pairs (conjugates implied) then one real root if n is odd; delta holds n */
@@ -423,6 +399,31 @@ MPGPU_DECL_ROOTS(dd)
 MPGPU_DECL_ROOTS(ddc)
 MPGPU_DECL_ROOTS(td)
 MPGPU_DECL_ROOTS(qd)
+
+/* ------------------------------------------------------------------------ */
+/* mp_roots_noalloc_qd: the QD batched root solver (mp_roots_qd) without a    */
+/* caller workspace, for code that cannot allocate device memory (a fixed     */
+/* memory pool that must not grow, a plugin whose allocator belongs to its    */
+/* host, a real-time loop where an allocation could stall).  The paper has no */
+/* counterpart; this is a library convenience.  Same arguments and same       */
+/* results (bit for bit) as mp_roots_qd without ws/ws_bytes.  Its workspace   */
+/* (queue counter and degree order) is a fixed 64.25 KiB device array inside  */
+/* the library, held by every GPU that loads the library until the process    */
+/* exits, so it takes npoly <= MP_NOALLOC_MAX_POLYS (16384) and              */
+/* opts->max_degree <= mp_roots_max_degree_qd() (no per-block slots); larger  */
+/* requests return MP_ENOMEM before anything is enqueued.  The first call on  */
+/* a device looks the array up (cudaGetSymbolAddress) for that device, so     */
+/* make it before any stream capture.  Concurrent calls from host threads are */
+/* safe on the host side (the lookup is guarded), but calls share the array: */
+/* calls whose kernels overlap on the GPU race on it.  The solve clears the   */
+/* queue counter itself; nothing else needs initialisation.  After            */
+/* cudaDeviceReset on a device, do not call it on that device again (the      */
+/* looked-up address is kept).                                                */
+/* ------------------------------------------------------------------------ */
+#define MP_NOALLOC_MAX_POLYS (1 << 14)
+mp_status mp_roots_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,
+                              const double *z0, int64_t pz0, double *roots, int64_t proots, int32_t *iters,
+                              int32_t *status, const mp_roots_opts *opts, mp_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Pipe-peak microbenchmark (measurement support, not part of the method):   */

@@ -29,8 +29,6 @@
 // each other.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "mp_arith.cuh"
 #include "mp_common.cuh"
 
@@ -635,75 +633,3 @@ MP_EXPORT_BUILD(td, P_td)
 MP_EXPORT_BUILD(qd, P_qd)
 
 }  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Horner adjoint for callers that cannot allocate device memory.
-//
-// Some callers cannot call cudaMalloc or pass in a workspace: code running
-// inside a pre-sized memory pool that must not grow, plugins and JIT hosts whose
-// allocator is owned by someone else, or a real-time loop where an allocation
-// could stall.  mp_polyeval_backward_noalloc_qd gives them the QD Horner adjoint
-// with its scratch in a fixed array that the library itself holds in device
-// memory.  It runs exactly the kernels of mp_polyeval_backward_qd, so its results
-// are the same bits.
-//
-// The scratch is MP_NOALLOC_MAX_POINTS QD values (4 MiB), allocated by the CUDA
-// runtime when the library is loaded and held by every GPU that loads it until
-// the process exits.  Calls share it: two calls whose kernels overlap on the GPU
-// (different streams, or a later call enqueued before an earlier one finished
-// with a stream that does not order them) race on it.  Nothing in it needs to
-// start at zero: every value the kernel reads was written earlier in the same
-// call.
-// ---------------------------------------------------------------------------
-
-// MP_NOALLOC_MAX_POINTS (131072 points) is defined in mpgpu.h.
-static __device__ __align__(256) double mp_noalloc_scratch[(size_t)MP_NOALLOC_MAX_POINTS * 4];
-
-namespace {
-
-// Device address of mp_noalloc_scratch, looked up once per device with that
-// device current (host code cannot use the array's name as a device pointer).
-// Host threads may call concurrently: the lookup and the cache are guarded by a
-// mutex.  The cache is not refreshed after cudaDeviceReset (which unloads the
-// library's device code and may move the array): a process that resets a device
-// must not call this entry point on that device again.
-mp_status noalloc_scratch(double **out)
-{
-    static std::mutex mu;
-    static double *addr[64] = {nullptr};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (dev < 0 || dev >= 64) return MP_EINVAL;
-    std::lock_guard<std::mutex> lock(mu);
-    if (addr[dev] == nullptr) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, mp_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_status(e);
-        addr[dev] = static_cast<double *>(p);
-    }
-    *out = addr[dev];
-    return MP_OK;
-}
-
-}  // namespace
-
-extern "C" mp_status mp_polyeval_backward_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef,
-                                                     int64_t pcoef, int64_t npts, const double *x, int64_t px,
-                                                     const double *dy, int64_t pdy, double *dcoef, int64_t pdc,
-                                                     double *dx, int64_t pdx, mp_stream s)
-{
-    if (npoly < 0 || npts < 0) return MP_EINVAL;
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    if (dcoef != nullptr && npoly > 0 && npts > 0) {
-        if (npoly > MP_NOALLOC_MAX_POINTS / npts) return MP_ENOMEM;  // npoly * npts too large
-        double *scratch = nullptr;
-        mp_status st = noalloc_scratch(&scratch);
-        if (st != MP_OK) return st;
-        ws = scratch;
-        ws_bytes = sizeof(double) * (size_t)MP_NOALLOC_MAX_POINTS * 4;
-    }
-    return polyeval_backward_launch<P_qd>(npoly, coef_off, coef, pcoef, npts, x, px, dy, pdy, dcoef, pdc, dx,
-                                          pdx, ws, ws_bytes, s);
-}

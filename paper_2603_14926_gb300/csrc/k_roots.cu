@@ -30,6 +30,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "mp_arith.cuh"
 #include "mp_common.cuh"
 
@@ -1145,3 +1147,72 @@ MP_EXPORT_ROOTS(td, P_td)
 MP_EXPORT_ROOTS(qd, P_qd)
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched roots for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc or pass in a workspace: code running
+// inside a pre-sized memory pool that must not grow, plugins and JIT hosts whose
+// allocator is owned by someone else, or a real-time loop where an allocation
+// could stall.  mp_roots_noalloc_qd gives them the QD Durand-Kerner solver with
+// its workspace (the persistent queue's counter and the degree order) in a
+// fixed array that the library itself holds in device memory.  It runs exactly
+// the kernels of mp_roots_qd, so its results are the same bits.
+//
+// The array is 256 + 4 * MP_NOALLOC_MAX_POLYS bytes (64.25 KiB), allocated by
+// the CUDA runtime when the library is loaded and held by every GPU that loads
+// it until the process exits.  Calls share it: two calls whose kernels overlap
+// on the GPU (different streams, or a later call enqueued before an earlier one
+// finished on a stream that does not order them) race on it.  Of its contents
+// only the queue counter must start at zero; the persistent launch clears it
+// (cudaMemsetAsync on the call's stream) before every solve, and the order
+// array is written before it is read in the same call.
+// ---------------------------------------------------------------------------
+
+// MP_NOALLOC_MAX_POLYS (16384 polynomials) is defined in mpgpu.h.
+static __device__ __align__(256) unsigned char mp_roots_noalloc_scratch[256 + 4 * (size_t)MP_NOALLOC_MAX_POLYS];
+
+namespace {
+
+// Device address of mp_roots_noalloc_scratch, looked up once per device with
+// that device current (host code cannot use the array's name as a device
+// pointer).  Host threads may call concurrently: the lookup and the cache are
+// guarded by a mutex.  The cache is not refreshed after cudaDeviceReset (which
+// unloads the library's device code and may move the array): a process that
+// resets a device must not call this entry point on that device again.
+mp_status roots_noalloc_scratch(void **out)
+{
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= 64) return MP_EINVAL;
+    std::lock_guard<std::mutex> lock(mu);
+    if (addr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, mp_roots_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" mp_status mp_roots_noalloc_qd(int64_t npoly, const int64_t *coef_off, const double *coef, int64_t pcoef,
+                                         const double *z0, int64_t pz0, double *roots, int64_t proots,
+                                         int32_t *iters, int32_t *status, const mp_roots_opts *opts, mp_stream s)
+{
+    if (npoly < 0 || opts == nullptr) return MP_EINVAL;
+    if (npoly > MP_NOALLOC_MAX_POLYS) return MP_ENOMEM;  // more order entries than the array holds
+    // above the shared-memory bound the solver keeps per-block slots in its workspace
+    if (opts->max_degree > dk_max_degree<P_qd>()) return MP_ENOMEM;
+    if (npoly == 0) return MP_OK;
+    void *ws = nullptr;
+    mp_status st = roots_noalloc_scratch(&ws);
+    if (st != MP_OK) return st;
+    return roots_launch<P_qd>(npoly, coef_off, coef, pcoef, z0, pz0, roots, proots, iters, status, opts, ws,
+                              sizeof(mp_roots_noalloc_scratch), s);
+}
