@@ -988,6 +988,38 @@ def roots_full_extra(prec="qd", npoly=4096, max_iter=1000, loop_polys=8, loop_ma
         "degrees": prob.degrees[sel].tolist(), "sweeps": itl.cpu().numpy().tolist(), "loop_s": tl,
         "identical_bits_to_batched": bool(same), "roots_per_s": float(prob.degrees[sel].sum()) / tl,
         "batched_over_loop_per_unit_work": (instr / tb) / (instr_l / tl)}
+    # the same sample as a host loop of one-sweep launches with a host flag check:
+    # per polynomial, launch after launch of one Jacobi sweep (mp_roots_P mode 1,
+    # max_iter 1) from the previous launch's iterate, the host reading the status
+    # after each; it stops at a converged or broken-down status, or at the sweep
+    # count the batched solve took (whose stagnation rule needs the history of
+    # delta that one-sweep launches do not keep)
+    sweeps_b = it[sel]
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    same_h, launches = True, 0
+    for q, b in enumerate(sel):
+        n = int(prob.degrees[b])
+        oq = dev(np.array([0, n + 1], dtype=np.int64))
+        cq = dev(sc[:, so[q]:so[q + 1]])
+        z = mpg.roots_init(prec, oq, cq, n, radius=1.1)
+        zb = torch.empty_like(z)
+        for _ in range(int(sweeps_b[q])):
+            zb, _itq, stq = mpg.roots(prec, oq, cq, n, z0=z, max_iter=1, mode=1, engine=engine, out=zb)
+            launches += 1
+            flag = int(stq.item())  # the host flag check (synchronizes)
+            z, zb = zb, z
+            if flag in (1, 3):
+                break
+        same_h &= np.array_equal(z.cpu().numpy().view(np.uint64),
+                                 np.ascontiguousarray(rh[:, prob.root_off[b]:prob.root_off[b + 1]]).view(np.uint64))
+    th = time.perf_counter() - h0
+    out["per_sweep_host_loop"] = {
+        "form": "per polynomial, a host loop of one-sweep launches (mp_roots_P mode 1, max_iter 1, z0 = the "
+                "previous iterate) with a host read of the status after each, through the Python binding",
+        "sample": out["per_poly_loop"]["sample"], "launches": launches, "loop_s": th,
+        "identical_bits_to_batched": bool(same_h), "roots_per_s": float(prob.degrees[sel].sum()) / th,
+        "batched_over_loop_per_unit_work": (instr / tb) / (instr_l / th)}
     # Eq. 5's own radius against radius 1.1 on a stratified subset of low degree
     small = np.where(prob.degrees <= eq5_max_degree)[0]
     small = small[np.argsort(prob.degrees[small], kind="stable")]

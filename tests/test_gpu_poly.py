@@ -144,6 +144,33 @@ def test_poly_from_roots_bit_exact(mp, oracle, prec):
     assert same_bits(host(got), want)
 
 
+def test_roots_one_sweep_host_loop_equals_batched(mp):
+    """The per-polynomial baseline of the benchmark: a host loop of one-sweep
+    launches (max_iter 1, z0 = the previous iterate, the status read after each)
+    ends, after the batched solve's sweep count, on the batched solve's bits."""
+    import torch
+
+    prob = inputs.dk_problem(14, 6, 10, 60)
+    coef = mp.poly_from_roots("qd", dev(prob.coef_off), dev(prob.rootdata), dev(prob.delta), 60,
+                              int(prob.coef_off[-1]))
+    r, it, st = mp.roots("qd", dev(prob.coef_off), coef, 60, radius=1.1, max_iter=200, sort=1)
+    r, it, st = host(r), host(it), host(st)
+    hc = host(coef)
+    for b in range(prob.npoly):
+        n = int(prob.degrees[b])
+        oq = dev(np.array([0, n + 1], dtype=np.int64))
+        cq = dev(hc[:, prob.coef_off[b]:prob.coef_off[b + 1]])
+        z = mp.roots_init("qd", oq, cq, n, radius=1.1)
+        zb = torch.empty_like(z)
+        for k in range(int(it[b])):
+            zb, _, sq = mp.roots("qd", oq, cq, n, z0=z, max_iter=1, mode=1, out=zb)
+            flag = int(sq.item())
+            z, zb = zb, z
+            if flag == 1:  # converged: only at the batched solve's last sweep
+                assert k + 1 == it[b] and st[b] == 1
+        assert same_bits(host(z), r[:, prob.root_off[b]:prob.root_off[b + 1]]), b
+
+
 @pytest.mark.parametrize("prec", ["dd", "qd"])
 @pytest.mark.parametrize("radius", [0.0, 1.1])
 def test_roots_init_bit_exact(mp, oracle, prec, radius):
