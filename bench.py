@@ -609,7 +609,25 @@ def extras(prec="qd", quick=False):
     bw = lambda i, mu: steps * 2 * i + npoly * npts * mu + npoly * npts * (deg + 1) * i  # noqa: E731
     out["horner_bwd"] = {"ms": tb * 1e3, "vs_fwd": tb / t,
                          **rates(bw(ins, mul_instr(prec)), bw(ins_paper, INSTR_MUL[prec]), tb)}
-    del off, coef, xs, dy
+    # the plain per-polynomial launch loop for the adjoint: one polyeval_backward
+    # call (both kernels) per polynomial, back to back on one stream, on a sample
+    # of 8 polynomials spread over the batch; same bits as the batched call
+    dcb, dxb = mpg.polyeval_backward(prec, off, coef, npts, xs, dy)
+    pick = np.linspace(0, npoly - 1, 8).astype(int)
+    off_q = torch.tensor([0, deg + 1], dtype=torch.int64, device="cuda")
+    parts = [(coef[:, q * (deg + 1):(q + 1) * (deg + 1)].contiguous(), xs[:, q * npts:(q + 1) * npts].contiguous(),
+              dy[:, q * npts:(q + 1) * npts].contiguous()) for q in pick]
+    res_q = []
+    tq = timed(lambda: res_q.append([mpg.polyeval_backward(prec, off_q, cq, npts, xq, dq) for cq, xq, dq in parts]),
+               reps=1)
+    same_q = all(torch.equal(dcq.view(torch.int64), dcb[:, q * (deg + 1):(q + 1) * (deg + 1)].view(torch.int64)) and
+                 torch.equal(dxq.view(torch.int64), dxb[:, q * npts:(q + 1) * npts].view(torch.int64))
+                 for q, (dcq, dxq) in zip(pick, res_q[-1]))
+    out["horner_bwd"]["per_poly_loop"] = {
+        "form": "one mp_polyeval_backward_P call per polynomial (its dx and dcoef kernels), back to back on one "
+                "stream", "polys": len(pick), "ms": tq * 1e3, "identical_bits_to_batched": bool(same_q),
+        "batched_over_loop_per_unit_work": (tq / len(pick)) / (tb / npoly)}
+    del off, coef, xs, dy, dcb, dxb, parts, res_q
     # GEMM adjoint through torch.autograd.Function: dA = dC B^T, dB = A^T dC
     from paper_2603_14926_gb300.autograd import mp_gemm
 
