@@ -367,7 +367,9 @@ typedef struct {
 mp_status mp_roots_hybrid_fallbacks(unsigned long long *count);
 
 /* mp_roots_init_P writes the Eq. 5 starting values (or radius-r circle) that */
-/* mp_roots_P uses when z0 == NULL, as a complex K-array (lower components 0). */
+/* mp_roots_P uses when z0 == NULL, as a complex K-array (lower components 0); */
+/* max_degree <= mp_roots_max_degree_P() (its kernel works in shared memory),  */
+/* else MP_EINVAL.                                                             */
 
 #define MPGPU_DECL_ALL(P, T)                                                                \
     MPGPU_DECL_EW(P, T)                                                                     \
