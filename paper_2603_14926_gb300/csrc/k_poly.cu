@@ -301,6 +301,34 @@ __device__ __forceinline__ typename P::V dx_point(int64_t n, const typename P::T
     return P::mul(dym, d, g);
 }
 
+// dx of point idx (polynomial idx / npts).
+template <class P>
+__device__ __forceinline__ void dx_one(int64_t idx, int64_t npts, const int64_t *__restrict__ coef_off,
+                                       const typename P::T *__restrict__ coef, int64_t pc,
+                                       const typename P::T *__restrict__ x, int64_t px,
+                                       const typename P::T *__restrict__ dy, int64_t pdy,
+                                       typename P::T *__restrict__ dx, int64_t pdx)
+{
+    using V = typename P::V;
+    const int64_t b = idx / npts;
+    const int64_t off = coef_off[b];
+    const int64_t n = coef_off[b + 1] - off - 1;
+    if (n < 0) {
+        vstore<P>(dx, pdx, idx, vzero<P>());
+        return;
+    }
+    const typename P::T *cb = coef + off;
+    const V xm = vload<P>(x, px, idx);
+    const V dym = vload<P>(dy, pdy, idx);
+    FastEngine<P> g;
+    V r = dx_point<P>(n, cb, pc, xm, dym, g);
+    if (g.failed()) {
+        NativeEngine<typename P::T> nat;
+        r = dx_point<P>(n, cb, pc, xm, dym, nat);
+    }
+    vstore<P>(dx, pdx, idx, r);
+}
+
 template <class P>
 __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *__restrict__ coef_off,
                                                  const typename P::T *__restrict__ coef, int64_t pc,
@@ -308,28 +336,10 @@ __global__ void __launch_bounds__(256) k_poly_dx(int64_t npoly, const int64_t *_
                                                  int64_t px, const typename P::T *__restrict__ dy,
                                                  int64_t pdy, typename P::T *__restrict__ dx, int64_t pdx)
 {
-    using V = typename P::V;
     const int64_t total = npoly * npts;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
-        const int64_t b = idx / npts;
-        const int64_t off = coef_off[b];
-        const int64_t n = coef_off[b + 1] - off - 1;
-        if (n < 0) {
-            vstore<P>(dx, pdx, idx, vzero<P>());
-            continue;
-        }
-        const typename P::T *cb = coef + off;
-        const V xm = vload<P>(x, px, idx);
-        const V dym = vload<P>(dy, pdy, idx);
-        FastEngine<P> g;
-        V r = dx_point<P>(n, cb, pc, xm, dym, g);
-        if (g.failed()) {
-            NativeEngine<typename P::T> nat;
-            r = dx_point<P>(n, cb, pc, xm, dym, nat);
-        }
-        vstore<P>(dx, pdx, idx, r);
-    }
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride)
+        dx_one<P>(idx, npts, coef_off, coef, pc, x, px, dy, pdy, dx, pdx);
 }
 
 // Warps per block of the coefficient adjoint.  One warp per polynomial and one
@@ -412,15 +422,14 @@ __device__ __forceinline__ bool dcoef_ring(int64_t n, int64_t off, int64_t base,
     return __any_sync(0xffffffffu, g.failed());
 }
 
+// The coefficient adjoint of polynomial b (one whole warp).
 template <class P>
-__global__ void __launch_bounds__(32 * DCOEF_WARPS)
-    k_poly_dcoef(int64_t npoly, const int64_t *__restrict__ coef_off, int64_t npts,
-                 const typename P::T *__restrict__ x, int64_t px, const typename P::T *__restrict__ dy,
-                 int64_t pdy, typename P::T *dcoef, int64_t pdc)
+__device__ __forceinline__ void dcoef_poly(int64_t b, int64_t npts, const int64_t *__restrict__ coef_off,
+                                           const typename P::T *__restrict__ x, int64_t px,
+                                           const typename P::T *__restrict__ dy, int64_t pdy,
+                                           typename P::T *dcoef, int64_t pdc)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t b = (int64_t)blockIdx.x * DCOEF_WARPS + (threadIdx.x >> 5);
-    if (b >= npoly) return;  // whole warp
     const int64_t off = coef_off[b];
     const int64_t n = coef_off[b + 1] - off - 1;
     if (n < 0) return;
@@ -441,6 +450,17 @@ __global__ void __launch_bounds__(32 * DCOEF_WARPS)
         NativeEngine<typename P::T> nat;
         dcoef_ring<P>(n, off, base, npts, x, px, dy, pdy, dcoef, pdc, nat);
     }
+}
+
+template <class P>
+__global__ void __launch_bounds__(32 * DCOEF_WARPS)
+    k_poly_dcoef(int64_t npoly, const int64_t *__restrict__ coef_off, int64_t npts,
+                 const typename P::T *__restrict__ x, int64_t px, const typename P::T *__restrict__ dy,
+                 int64_t pdy, typename P::T *dcoef, int64_t pdc)
+{
+    const int64_t b = (int64_t)blockIdx.x * DCOEF_WARPS + (threadIdx.x >> 5);
+    if (b >= npoly) return;  // whole warp
+    dcoef_poly<P>(b, npts, coef_off, x, px, dy, pdy, dcoef, pdc);
 }
 
 // The adjoint needs no workspace: the coefficient sweep parks its partial sums
