@@ -167,24 +167,24 @@ def test_gemm_benchmark_sizes_sampled(mp, oracle, prec, n):
         assert same_bits(C[:, i, j], want), (i, j)
 
 
-def test_roots_above_shared_memory_bound(mp, oracle):
-    """Degrees above the shared-memory bound: each block keeps its coefficients and
-    iterate in a slot of the workspace.  A degree-2600 QD polynomial, two sweeps,
-    persistent launch and per-polynomial launch, equals the oracle; smaller
-    polynomials solved in the same launch equal their shared-memory solve."""
-    bound = mp.roots_max_degree("qd")
-    n = 2600
-    assert n > bound
+@pytest.mark.parametrize("prec,n", [("qd", 2600), ("dd", 4900)])
+def test_roots_above_shared_memory_bound(mp, oracle, prec, n):
+    """Degrees above the shared-memory bound (QD 2421, DD 4843): each block keeps
+    its coefficients and iterate in a slot of the workspace.  A polynomial above
+    the bound, two sweeps, persistent launch and per-polynomial launch, equals
+    the oracle; smaller polynomials solved in the same launch equal their
+    shared-memory solve."""
+    assert n > mp.roots_max_degree(prec)
     prob = inputs.dk_problem(9, 1, n, n)
-    coef = oracle.poly_from_roots("qd", prob)
-    wr, wit, wst = oracle.roots("qd", prob.coef_off, coef, radius=1.1, max_iter=2)
+    coef = oracle.poly_from_roots(prec, prob)
+    wr, wit, wst = oracle.roots(prec, prob.coef_off, coef, radius=1.1, max_iter=2)
     for mode in (0, 1):
-        r, it, st = mp.roots("qd", dev(prob.coef_off), dev(coef), n, radius=1.1, max_iter=2, mode=mode)
+        r, it, st = mp.roots(prec, dev(prob.coef_off), dev(coef), n, radius=1.1, max_iter=2, mode=mode)
         assert host(it)[0] == wit[0] == 2 and host(st)[0] == wst[0], mode
         assert same_bits(host(r), wr), mode
     small = inputs.dk_problem(10, 6, 20, 200)
-    cs = dev(oracle.poly_from_roots("qd", small))
-    r1, i1, s1 = mp.roots("qd", dev(small.coef_off), cs, 200, radius=1.1, max_iter=30)
-    r2, i2, s2 = mp.roots("qd", dev(small.coef_off), cs, n, radius=1.1, max_iter=30)  # slots
+    cs = dev(oracle.poly_from_roots(prec, small))
+    r1, i1, s1 = mp.roots(prec, dev(small.coef_off), cs, 200, radius=1.1, max_iter=30)
+    r2, i2, s2 = mp.roots(prec, dev(small.coef_off), cs, n, radius=1.1, max_iter=30)  # slots
     assert np.array_equal(host(i1), host(i2)) and np.array_equal(host(s1), host(s2))
     assert same_bits(host(r1), host(r2))
