@@ -301,9 +301,11 @@ const char *mp_version(void);
 /* and statuses are bit-identical to the CPU oracle and identical between   */
 /* the persistent batched launch (mode 0), one launch per polynomial        */
 /* (mode 1) and the cluster solve (mode 2: one thread-block cluster of      */
-/* C = max(2, ceil(max_degree/32)) <= 8 CTAs per polynomial, each CTA owning */
-/* ceil(n/C) roots, every complex step split over a lane pair, the new      */
-/* iterate exchanged through distributed shared memory once per sweep; for  */
+/* C <= 8 CTAs per polynomial, each CTA owning ceil(n/C) roots: up to       */
+/* max_degree 128, C = max(2, ceil(max_degree/16)) and every complex step   */
+/* split over a lane quad, above it C = ceil(max_degree/32) and a lane      */
+/* pair; the new iterate exchanged through distributed shared memory once   */
+/* per sweep; for                                                           */
 /* the latency of few polynomials; max_degree <= 256 and sort = 0, else     */
 /* MP_EINVAL), and between the engines: the hybrid engine (opts->engine 0 = */
 /* automatic, or 1) runs each root's update with TwoSum error terms on the  */

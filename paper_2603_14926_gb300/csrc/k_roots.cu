@@ -739,7 +739,90 @@ __device__ __forceinline__ void dk_product_pair(const double *z, int64_t zc, int
     }
 }
 
+// The same two steps split over a lane quad (role 0..3 = lane & 3): each lane
+// forms one of the four real products of the complex product, the quad swaps
+// them in pairs (roles 0 <-> 1, 2 <-> 3) to form the real part (roles 0, 1:
+// t1 - t2) and the imaginary part (roles 2, 3: t3 + t4) in the one-lane
+// order, and a second swap (roles 0 <-> 2, 1 <-> 3) hands both parts to every
+// lane.  Lanes that form the same part form it from the same operands, so they
+// agree bit for bit.  One multiply per lane and step instead of two.
+template <class P> __device__ __forceinline__ typename P::V quad_swap(const typename P::V &v, int mask)
+{
+    typename P::V r;
+#pragma unroll
+    for (int c = 0; c < P::K; c++) r.c[c] = __shfl_xor_sync(0xffffffffu, v.c[c], mask);
+    return r;
+}
+
 template <class P, class E>
+__device__ __forceinline__ void dk_horner_quad(const double *c, int64_t cap, int64_t kk, const typename P::V &zr,
+                                               const typename P::V &zi, typename P::V &hr, typename P::V &hi,
+                                               long long &Eq, int role, E &g)
+{
+    using V = typename P::V;
+    V a = vload<P>(c, cap, kk);
+    if (Eq > 1000) a = vzero<P>();
+    else if (Eq > 0) vscale<P>(a, (int)-Eq);
+    // role 0: t1 = hr zr, 1: t2 = hi zi, 2: t3 = hr zi, 3: t4 = hi zr
+    const V t = P::mul((role & 1) ? hi : hr, (role == 1 || role == 2) ? zi : zr, g);
+    const V o = quad_swap<P>(t, 1);
+    // roles 0, 1: t1 + (-t2); roles 2, 3: t3 + t4 -- one add for the whole warp
+    const V x = (role & 1) ? o : t, y = (role & 1) ? t : o;
+    V w = P::add(x, role < 2 ? vneg<P>(y) : y, g);
+    if (role < 2) w = P::add(w, a, g);
+    const V ow = quad_swap<P>(w, 2);
+    hr = role < 2 ? w : ow;
+    hi = role < 2 ? ow : w;
+    const int be = max(bexp(hr.c[0]), bexp(hi.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(hr, -DK_RESCALE);
+        vscale<P>(hi, -DK_RESCALE);
+        Eq += DK_RESCALE;
+    }
+}
+
+template <class P, class E>
+__device__ __forceinline__ void dk_product_quad(const double *z, int64_t zc, int64_t j, bool take,
+                                                const typename P::V &zr, const typename P::V &zi, typename P::V &dr,
+                                                typename P::V &di, long long &Ed, int role, E &g)
+{
+    using V = typename P::V;
+    constexpr int K = P::K;
+    const uint32_t bad0 = g.bad_flags();
+    // roles 0, 2: tr = zr - z_j (real), roles 1, 3: ti = zi - z_j (imaginary)
+    const int part = role & 1;
+    const V d = vsub<P>(part ? zi : zr, vload<P>(z + (part ? K * zc : 0), zc, j), g);
+    const V od = quad_swap<P>(d, 1);
+    const V tr = part ? od : d, ti = part ? d : od;
+    // role 0: t1 = dr tr, 1: t2 = di ti, 2: t3 = dr ti, 3: t4 = di tr
+    const V t = P::mul((role & 1) ? di : dr, (role == 1 || role == 2) ? ti : tr, g);
+    const V o = quad_swap<P>(t, 1);
+    // roles 0, 1: t1 + (-t2); roles 2, 3: t3 + t4 -- one add for the whole warp
+    const V x = (role & 1) ? o : t, y = (role & 1) ? t : o;
+    const V w = P::add(x, role < 2 ? vneg<P>(y) : y, g);
+    const V ow = quad_swap<P>(w, 2);
+    V nr = role < 2 ? w : ow, ni = role < 2 ? ow : w;
+    long long nE = Ed;
+    const int be = max(bexp(nr.c[0]), bexp(ni.c[0]));
+    if (be >= 1023 + DK_RESCALE + 1) {
+        vscale<P>(nr, -DK_RESCALE);
+        vscale<P>(ni, -DK_RESCALE);
+        nE += DK_RESCALE;
+    } else if (be <= 1023 - DK_RESCALE - 1 && (nr.c[0] != 0.0 || ni.c[0] != 0.0)) {
+        vscale<P>(nr, DK_RESCALE);
+        vscale<P>(ni, DK_RESCALE);
+        nE -= DK_RESCALE;
+    }
+    if (take) {
+        dr = nr;
+        di = ni;
+        Ed = nE;
+    } else {
+        g.set_bad_flags(bad0);
+    }
+}
+
+template <class P, class E, int L>
 __global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
 {
     namespace cg = cooperative_groups;
@@ -765,7 +848,7 @@ __global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
         return;
     }
     const int64_t cap = (int64_t)A.max_degree + 1, zc = A.max_degree;
-    const int64_t m = (n + C - 1) / C;                  // roots per CTA (<= 32)
+    const int64_t m = (n + C - 1) / C;                  // roots per CTA (<= 64 / L)
     double *c = dk_smem;                                // K planes
     double *zbuf[2] = {c + K * cap, c + K * cap + 2 * K * zc};  // 2K planes each
     double *pbuf = c + K * cap + 4 * K * zc;            // 2K planes of m: the products
@@ -777,10 +860,10 @@ __global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
 
     const int64_t r0 = (int64_t)rank * m;
     const int64_t cnt = n - r0 < m ? (n - r0 > 0 ? n - r0 : 0) : m;  // roots this CTA owns
-    const int hw = (int)((2 * m + 31) / 32);            // warps of Horner pairs, then as many of product pairs
-    const int warp = tid >> 5, im = tid & 1;
+    const int hw = (int)((L * m + 31) / 32);            // warps of Horner lane groups, then as many of product ones
+    const int warp = tid >> 5, im = tid & (L - 1);      // a lane's role within its group
     const bool horner = warp < hw, prod = !horner && warp < 2 * hw;
-    const int64_t q = horner ? tid / 2 : (tid - 32 * hw) / 2;   // pair index within the CTA
+    const int64_t q = horner ? tid / L : (tid - 32 * hw) / L;   // group (root) index within the CTA
     const bool valid = (horner || prod) && q < cnt;
     const int64_t i = cnt > 0 ? r0 + (q < cnt ? q : cnt - 1) : 0;  // ghost pairs repeat a valid root
 
@@ -799,8 +882,12 @@ __global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
         if (prod) {
             V dr = vone<P>(), di = vzero<P>();
             long long Ed = 0;
-            for (int64_t j = 0; j < n; j++) dk_product_pair<PU>(z, zc, j, j != i, zr, zi, dr, di, Ed, im, g);
-            const uint32_t fb = g.bad_flags() | __shfl_xor_sync(0xffffffffu, g.bad_flags(), 1);
+            if (L == 4)
+                for (int64_t j = 0; j < n; j++) dk_product_quad<PU>(z, zc, j, j != i, zr, zi, dr, di, Ed, im, g);
+            else
+                for (int64_t j = 0; j < n; j++) dk_product_pair<PU>(z, zc, j, j != i, zr, zi, dr, di, Ed, im, g);
+            uint32_t fb = g.bad_flags() | __shfl_xor_sync(0xffffffffu, g.bad_flags(), 1);
+            if (L == 4) fb |= __shfl_xor_sync(0xffffffffu, fb, 2);
             if (valid && !im) {
                 vstore<P>(pbuf, m, q, dr);
                 vstore<P>(pbuf + K * m, m, q, di);
@@ -809,8 +896,12 @@ __global__ void __launch_bounds__(DK_CLUSTER_THREADS) k_dk_cluster(DKArgs<P> A)
             }
         } else if (horner) {
             hr = vload<P>(c, cap, n);
-            for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_pair<PU>(c, cap, kk, zr, zi, hr, hi, Eq, im, g);
+            if (L == 4)
+                for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_quad<PU>(c, cap, kk, zr, zi, hr, hi, Eq, im, g);
+            else
+                for (int64_t kk = n - 1; kk >= 0; kk--) dk_horner_pair<PU>(c, cap, kk, zr, zi, hr, hi, Eq, im, g);
             hbad = g.bad_flags() | __shfl_xor_sync(0xffffffffu, g.bad_flags(), 1);
+            if (L == 4) hbad |= __shfl_xor_sync(0xffffffffu, hbad, 2);
         }
         __syncthreads();  // the products are in place
         double dmax = 0.0, zm = 0.0;
@@ -964,11 +1055,16 @@ template <class P> static size_t dk_ws_deg(int64_t npoly, int32_t max_degree)
 }
 
 // The persistent batched launch (mode 0) or one launch per polynomial (mode 1).
-// Cluster size for a cluster solve: one CTA per 32 roots of the largest
-// degree, at least 2, at most DK_CLUSTER_MAX (0 when the degree is too large).
+// Lanes per root of a cluster solve: four (one real product of each complex
+// product per lane) while one CTA per 16 roots fits in a portable cluster, else
+// two.  Cluster size: one CTA per 64 / lanes roots of the largest degree, at
+// least 2, at most DK_CLUSTER_MAX (0 when the degree is too large).
+static int dk_cluster_lanes(int32_t max_degree) { return max_degree <= 16 * DK_CLUSTER_MAX ? 4 : 2; }
+
 static int dk_cluster_size(int32_t max_degree)
 {
-    const int c = (max_degree + 31) / 32;
+    const int per = 64 / dk_cluster_lanes(max_degree);
+    const int c = (max_degree + per - 1) / per;
     if (c > DK_CLUSTER_MAX) return 0;
     return c < 2 ? 2 : c;
 }
@@ -986,9 +1082,11 @@ static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npol
 {
     if (o->mode == 2) {
         const int C = dk_cluster_size(o->max_degree);
+        const int L = dk_cluster_lanes(o->max_degree);
         const size_t cs = dk_cluster_smem<P>(o->max_degree, C);
         if (C == 0 || npoly * C > 0x7fffffff) return MP_EINVAL;
-        cudaError_t e = cudaFuncSetAttribute(k_dk_cluster<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+        auto kern = L == 4 ? k_dk_cluster<P, E, 4> : k_dk_cluster<P, E, 2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
         if (e != cudaSuccess) return cuda_status(e);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(npoly * C), 1, 1);
@@ -1002,7 +1100,7 @@ static mp_status dk_run(const DKArgs<P> &A, const mp_roots_opts *o, int64_t npol
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cuda_status(cudaLaunchKernelEx(&cfg, k_dk_cluster<P, E>, A));
+        return cuda_status(cudaLaunchKernelEx(&cfg, kern, A));
     }
     if (o->mode == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_dk_persistent<P, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,6 +1,6 @@
 """GPU: the Durand-Kerner cluster solve (mp_roots_P mode 2) -- one polynomial per
 thread-block cluster, its roots spread over the cluster's SMs and each complex
-step split over a lane pair -- gives the bits of the one-block solver and of
+step split over a lane quad (degrees <= 128) or pair -- gives the bits of the one-block solver and of
 the oracle: roots, sweep counts and statuses (Section 4.2, Eq. 4)."""
 
 import numpy as np
@@ -31,12 +31,15 @@ def test_cluster_chebyshev_bit_exact(mp, oracle, prec, n):
 
 
 @pytest.mark.parametrize("engine", [0, 2])
-def test_cluster_random_batch_matches_block_solver(mp, oracle, engine):
-    """Random-root polynomials of degrees 1..256 (cluster sizes 2..8, ragged root
-    counts per CTA, CTAs owning no root): every root, sweep count and status equal
-    to the persistent one-block solve's; the three smallest also to the oracle's."""
+@pytest.mark.parametrize("dmax", [128, 256])
+def test_cluster_random_batch_matches_block_solver(mp, oracle, engine, dmax):
+    """Random-root polynomials of degrees 1..dmax (lane quads per root and one CTA
+    per 16 roots up to degree 128, lane pairs and one CTA per 32 roots above;
+    ragged root counts per CTA, CTAs owning no root): every root, sweep count and
+    status equal to the persistent one-block solve's; the three smallest also to
+    the oracle's."""
     prec = "qd"
-    prob = inputs.dk_problem(6, 12, 1, 256)
+    prob = inputs.dk_problem(6, 12, 1, dmax)
     coef = oracle.poly_from_roots(prec, prob)
     md = int(prob.degrees.max())
     kw = dict(radius=1.1, max_iter=40)
