@@ -1101,7 +1101,8 @@ def chebyshev_extra(prec="qd", n=64, copies=4096, engine=0):
     e1.record()
     torch.cuda.synchronize()
     tc = e0.elapsed_time(e1) / 1e3
-    cluster = {"single_solve_gpu_s": tc, "cluster_ctas": max(2, (n + 31) // 32),
+    lanes = 4 if n <= 128 else 2  # lanes per root and CTAs per cluster as the library picks them
+    cluster = {"single_solve_gpu_s": tc, "cluster_ctas": max(2, -(-n // (64 // lanes))), "lanes_per_root": lanes,
                "identical_bits": bool(torch.equal(rc.view(torch.int64), r.view(torch.int64)) and
                                       torch.equal(itc, it) and torch.equal(stc, st)),
                "speedup_over_one_block": t1 / tc}

@@ -340,7 +340,8 @@ typedef struct {
     double radius;           /* > 0: start circle radius instead of Eq. 5's */
     int64_t watchdog_cycles; /* > 0: per-polynomial clock64 budget, status 3 when spent */
     int32_t max_degree;      /* host bound on every degree, required */
-    int32_t threads;         /* threads per block: 0 = 256 (hybrid) or 128 (engine 2); else a multiple of 32, <= 256 */
+    int32_t threads;         /* threads per block: 0 = automatic (hybrid: the smallest multiple of 64 that is
+                                >= 2 * max_degree, at most 256; engine 2: 128); else a multiple of 32, <= 256 */
     int32_t blocks_per_sm;   /* persistent grid = SMs * blocks_per_sm, 0 = automatic */
     int32_t sort;            /* 1: process polynomials in descending degree (default 0 = off) */
     int32_t engine;          /* 0: automatic (hybrid), 1: hybrid, 2: FP64 pipe throughout; same bits */
