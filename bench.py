@@ -1292,8 +1292,8 @@ def run_gpu(a, rank, world, pool):
     peak_nominal = NOMINAL_FP64_TFLOPS * 1e12 / 2 / 1e9  # G FP64 instructions/s
     achieved = instr / launch_s / 1e9
     peak_live = fp64_peak_live() / 1e9
-    kernel = (f"k_gemm_tma<P_{prec}, HybridEngine<false>, 2, 32, 32, 16, 2, 2> (TMA-staged tiles; TwoSum error "
-              f"terms on the integer pipes, every other step on the FP64 pipe)" if hybrid else
+    kernel = (f"k_gemm_tma<P_{prec}, HybridEngine<false>, 2, 16, 16, 16, 1, 1> (TMA-staged 16x16 tiles, one output "
+              f"per thread; TwoSum error terms on the integer pipes, every other step on the FP64 pipe)" if hybrid else
               f"k_gemm_tma<P_{prec}, NativeEngine<double>, 2, 32, 32, 16, 2, 2> (TMA-staged tiles; FP64 pipe)")
     roofline = {"bound": "alu", "kernel": kernel,
                 "achieved": achieved,

@@ -409,11 +409,15 @@ static mp_status gemm_run_tma(int opA, int opB, int64_t m, int64_t n, int64_t k,
     return launch_status();
 }
 
-// Tile configurations.  Binary64 precisions are FP64-pipe bound, so a few
-// independent chains per thread suffice; the TMA-staged 32x32 tile is their
-// built-in choice (it runs at the same rate as plain loads).  For binary32 the
-// 32x32 tile with 2x2 micro-tiles measured fastest (QF n = 2048: 34.1 T FP32
-// instructions/s against 29.5 T for 64x64).
+// Tile configurations.  Binary64 precisions are FP64-pipe bound, so one chain
+// per thread suffices: the built-in choice is the TMA-staged 16x16 tile with one
+// output per thread on the hybrid engine (configuration 10).  At QD n = 2048 it
+// issues FP64 work at the rate DFMA chains reach (1594 ms against 1692 ms for
+// 32x32 tiles with 2x2 micro-tiles, whose four chains per thread spill at the
+// two-blocks-per-SM register budget; n = 1024: 199.5 against 224.3 ms, where
+// its 16384 tiles also fill the last wave).  Same bits in every configuration.
+// For binary32 the 32x32 tile with 2x2 micro-tiles measured fastest (QF
+// n = 2048: 34.1 T FP32 instructions/s against 29.5 T for 64x64).
 template <class P, bool F64 = P::fp64> struct GemmTable;
 
 template <class P> struct GemmTable<P, true> {
@@ -421,7 +425,7 @@ template <class P> struct GemmTable<P, true> {
     using H = HybridEngine<false>;
     using HQ = HybridEngine<true>;
     using HP = HybridEngine<false, true>;
-    static constexpr int count = 10;
+    static constexpr int count = 11;
     static const char *name(int c)
     {
         switch (c) {
@@ -435,10 +439,11 @@ template <class P> struct GemmTable<P, true> {
         case 7: return "BM32 BN32 BK16 TM2 TN2 (256 thr), hybrid TwoSum";
         case 8: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum, 1 block/SM register budget";
         case 9: return "BM32 BN32 BK16 TM2 TN2 (256 thr), TMA, hybrid TwoSum + TwoProd";
+        case 10: return "BM16 BN16 BK16 TM1 TN1 (256 thr), TMA, hybrid TwoSum (integer error term)";
         }
         return nullptr;
     }
-    static constexpr int fallback = 5;  // configuration used for config = -1
+    static constexpr int fallback = 10;  // configuration used for config = -1
     template <typename... Args> static mp_status run(int c, Args... a)
     {
         switch (c) {
@@ -451,6 +456,7 @@ template <class P> struct GemmTable<P, true> {
         case 7: return gemm_run<P, H, 2, 32, 32, 16, 2, 2>(a...);
         case 8: return gemm_run_tma<P, H, 1, 32, 32, 16, 2, 2>(a...);
         case 9: return gemm_run_tma<P, HP, 2, 32, 32, 16, 2, 2>(a...);
+        case 10: return gemm_run_tma<P, H, 2, 16, 16, 16, 1, 1>(a...);
         default: return gemm_run<P, N, 2, 32, 32, 16, 2, 2>(a...);
         }
     }
